@@ -1,0 +1,523 @@
+/*
+ * FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY (see lbm_oracle.h for scope,
+ * citations and readings).  Plain loops in the paper's order: per node,
+ * macroscopic quantities -> moments -> relaxation -> back to velocity space,
+ * then push-streaming with the wall rules.  No blocking, fusion or reordering.
+ */
+#include "lbm_oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---- lattice definitions ------------------------------------------------ */
+
+/* Eq. 8: D2Q9 velocities, c = 1.  The first five are the D2Q5 set (Sec. 3.2). */
+static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+/* Eq. 20: D2Q9 weights */
+static const double W9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+/* Eq. 13: transformation matrix M (rows: rho, e, eps, jx, qx, jy, qy, pxx, pxy) */
+static const double M9[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},
+    {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},
+    {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+
+/* Eq. 23: D2Q5 transformation matrix N */
+static const double N5[5][5] = {
+    {1, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0},
+    {0, 0, 1, 0, -1},
+    {-4, 1, 1, 1, 1},
+    {0, 1, -1, 1, -1}};
+
+static double M9inv[9][9];
+static double N5inv[5][5];
+static int inverses_ready = 0;
+
+/* index of the opposite velocity */
+static int opposite(int q)
+{
+    for (int k = 0; k < 9; ++k)
+        if (EX[k] == -EX[q] && EY[k] == -EY[q]) return k;
+    return -1;
+}
+
+/* Gauss-Jordan inversion with partial pivoting (n <= 9). The paper defines
+ * f* = M^-1 m* (Eq. 11); the inverse is computed, not written down. */
+static void invert(int n, const double* a, double* inv)
+{
+    double w[9][18];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c)
+            w[r][c] = c < n ? a[r * n + c] : (c - n == r ? 1.0 : 0.0);
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (fabs(w[r][col]) > fabs(w[piv][col])) piv = r;
+        if (piv != col)
+            for (int c = 0; c < 2 * n; ++c) {
+                double t = w[col][c];
+                w[col][c] = w[piv][c];
+                w[piv][c] = t;
+            }
+        double d = w[col][col];
+        for (int c = 0; c < 2 * n; ++c) w[col][c] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            double m = w[r][col];
+            if (m == 0.0) continue;
+            for (int c = 0; c < 2 * n; ++c) w[r][c] -= m * w[col][c];
+        }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) inv[r * n + c] = w[r][n + c];
+}
+
+static void ensure_inverses(void)
+{
+    if (inverses_ready) return;
+    invert(9, &M9[0][0], &M9inv[0][0]);
+    invert(5, &N5[0][0], &N5inv[0][0]);
+    inverses_ready = 1;
+}
+
+/* ---- parameters (Sec. 4, Sec. 4.1, Eqs. 7, 14, 29) ------------------------- */
+
+int or_derive(or_params* p)
+{
+    if (p->nx < 3 || p->ny < 3) return 1;
+    if (!(p->eps > 0.0 && p->eps <= 1.0) || !(p->Da > 0.0) || !(p->Ra > 0.0) || !(p->Pr > 0.0) ||
+        !(p->Le > 0.0) || !(p->J > 0.0) || !(p->sigma > 0.0))
+        return 1;
+    if (p->Ma <= 0.0) p->Ma = 0.1;          /* Sec. 4.1: Ma = 0.1 */
+    if (p->varpi <= 0.0) p->varpi = 0.4;    /* Sec. 4: varpi = 2/5 */
+    double L = (double)p->nx;               /* Sec. 4.1: L = N_x in lattice units */
+    p->rho0 = 1.0;
+    p->cs2 = 1.0 / 3.0;                     /* c_s = c / sqrt(3) */
+    p->U = p->Ma * sqrt(p->cs2);            /* Ma = U / c_s */
+    /* 1/s_nu = 1/2 + Ma J L sqrt(Pr) / (c_s sqrt(Ra)), i.e. nu_e = J U L sqrt(Pr/Ra) */
+    double inv_snu = 0.5 + p->Ma * p->J * L * sqrt(p->Pr) / (sqrt(p->cs2) * sqrt(p->Ra));
+    p->nu_e = p->cs2 * (inv_snu - 0.5);     /* nu_e = c_s^2 (1/s_nu - 1/2) */
+    p->nu = p->nu_e / p->J;                 /* J = nu_e / nu */
+    p->alpha_e = p->nu / p->Pr;             /* Pr = nu / alpha_e */
+    p->D_e = p->alpha_e / p->Le;            /* Le = alpha_e / D_e */
+    p->csT2 = p->varpi / 2.0;               /* c_sT^2 = varpi / 2 */
+    p->K = p->Da * L * L;                   /* Da = K / L^2 */
+    p->Feps = 1.75 / sqrt(150.0 * p->eps * p->eps * p->eps); /* Eq. 7 */
+    p->gbT = p->U * p->U / L;               /* U = sqrt(g beta_T dT L), dT = 1 */
+    p->gbC = p->N * p->gbT;                 /* N = beta_C dC / (beta_T dT), dC = dT = 1 */
+    p->T0 = 0.5;                            /* T0 = (T_h + T_l)/2 with T_h = 1, T_l = 0 */
+    p->C0 = 0.5;
+    /* Sec. 4: s0 = s3 = s5 = 1, s1 = s2 = 1.1, s4 = s6 = 1.2; s7 = s8 = s_nu */
+    double snu = 1.0 / inv_snu;
+    double rates[9] = {1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2, snu, snu};
+    memcpy(p->s, rates, sizeof rates);
+    /* Eq. 29: alpha_e = c_sT^2 (1/zeta_a - 1/2), D_e = c_sT^2 (1/eta_D - 1/2) */
+    double za = 1.0 / (0.5 + p->alpha_e / p->csT2);
+    double eD = 1.0 / (0.5 + p->D_e / p->csT2);
+    double z[5] = {1.0, za, za, 1.5, 1.5};  /* zeta_0 = 1, zeta_3 = zeta_4 = 1.5 */
+    double e[5] = {1.0, eD, eD, 1.5, 1.5};  /* eta_0 = 1, eta_3 = eta_4 = 1.5 */
+    memcpy(p->zeta, z, sizeof z);
+    memcpy(p->eta, e, sizeof e);
+    p->scalar_lr = OR_DIRICHLET;
+    p->scalar_tb = OR_ADIABATIC;
+    p->Tw[0] = 1.0; p->Tw[1] = 0.0;
+    p->Cw[0] = 1.0; p->Cw[1] = 0.0;
+    p->Gx = 0.0;
+    for (int k = 0; k < 9; ++k) if (!(p->s[k] > 0.0 && p->s[k] < 2.0)) return 2;
+    for (int k = 0; k < 5; ++k)
+        if (!(p->zeta[k] > 0.0 && p->zeta[k] < 2.0) || !(p->eta[k] > 0.0 && p->eta[k] < 2.0))
+            return 2;
+    return 0;
+}
+
+/* ---- state ---------------------------------------------------------------- */
+
+struct or_state {
+    or_params p;
+    long t;
+    size_t n;
+    double *f, *g, *h, *hist;   /* pre-collision distributions at time t */
+    double *f2, *g2, *h2;       /* streaming targets */
+};
+
+long or_time(const or_state* s) { return s->t; }
+
+/* SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the state advances by the
+ * golden-ratio increment and each output is the mix of the state.  The k-th
+ * output of a generator seeded with `seed` is mix(seed + (k+1)*gamma). */
+static uint64_t splitmix64_at(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + (k + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double or_uniform(uint64_t seed, uint64_t k)
+{
+    return (double)(splitmix64_at(seed, k) >> 11) * (1.0 / 9007199254740992.0); /* 2^-53 */
+}
+
+/* ---- per-node method -------------------------------------------------------- */
+
+typedef struct {
+    double rho, jx, jy, T, C, Gx, Gy, ux, uy, Fx, Fy;
+} or_macro;
+
+/* Eqs. 16, 26, 6, 19, 18, 5 in that order. */
+static void macro(const or_params* p, const double f[9], const double g[5], const double h[5],
+                  or_macro* o)
+{
+    double rho = 0, jx = 0, jy = 0;
+    for (int i = 0; i < 9; ++i) {
+        rho += f[i];                               /* Eq. 16 */
+        jx += EX[i] * f[i];                        /* sum e_i f_i */
+        jy += EY[i] * f[i];
+    }
+    double sg = 0, sh = 0;
+    for (int i = 0; i < 5; ++i) { sg += g[i]; sh += h[i]; }
+    double T = sg / p->sigma;                      /* Eq. 26: sigma T = sum g */
+    double C = sh / p->eps;                        /* Eq. 26: eps C = sum h */
+    double Gx = p->Gx;                             /* external, test-only */
+    double Gy = p->gbT * (T - p->T0) + p->gbC * (C - p->C0);   /* Eq. 6 */
+    double eps = p->eps;
+    /* Eq. 19 (delta_t = 1) */
+    double vx = jx / p->rho0 + 0.5 * eps * Gx;
+    double vy = jy / p->rho0 + 0.5 * eps * Gy;
+    double l0 = 0.5 * (1.0 + eps * 0.5 * p->nu / p->K);
+    double l1 = eps * 0.5 * p->Feps / sqrt(p->K);
+    double vmag = sqrt(vx * vx + vy * vy);
+    /* Eq. 18 */
+    double den = l0 + sqrt(l0 * l0 + l1 * vmag);
+    double ux = vx / den, uy = vy / den;
+    /* Eq. 5 */
+    double umag = sqrt(ux * ux + uy * uy);
+    double Fx = -eps * p->nu / p->K * ux - eps * p->Feps / sqrt(p->K) * umag * ux + eps * Gx;
+    double Fy = -eps * p->nu / p->K * uy - eps * p->Feps / sqrt(p->K) * umag * uy + eps * Gy;
+    o->rho = rho; o->jx = jx; o->jy = jy; o->T = T; o->C = C; o->Gx = Gx; o->Gy = Gy;
+    o->ux = ux; o->uy = uy; o->Fx = Fx; o->Fy = Fy;
+}
+
+/* D2Q5 collision (Eqs. 21/22 with Eqs. 24/25 and 27) for a scalar Phi whose
+ * zeroth moment carries the factor `cap` (sigma for T, eps for C). */
+static void collide_d2q5(const or_params* p, const double rates[5], double cap, double Phi,
+                         double ux, double uy, double Xx, double Xy, const double d[5],
+                         double ds[5])
+{
+    double varpi = p->varpi;
+    double wt[5] = {1.0 - varpi, varpi / 4, varpi / 4, varpi / 4, varpi / 4};
+    /* Eq. 27: S~_i = w~_i e_i . d(Phi u)/dt / c_sT^2, then S = N S~ */
+    double St[5], S[5];
+    for (int i = 0; i < 5; ++i) St[i] = wt[i] * (EX[i] * Xx + EY[i] * Xy) / p->csT2;
+    for (int k = 0; k < 5; ++k) {
+        S[k] = 0;
+        for (int i = 0; i < 5; ++i) S[k] += N5[k][i] * St[i];
+    }
+    /* n = N d */
+    double n[5];
+    for (int k = 0; k < 5; ++k) {
+        n[k] = 0;
+        for (int i = 0; i < 5; ++i) n[k] += N5[k][i] * d[i];
+    }
+    /* Eqs. 24/25: modified equilibrium moments */
+    double neq[5] = {cap * Phi, ux * Phi, uy * Phi, -4.0 * cap * Phi + 5.0 * varpi * Phi, 0.0};
+    /* n* = n - Theta (n - n_eq) + (I - Theta/2) S */
+    double ns[5];
+    for (int k = 0; k < 5; ++k)
+        ns[k] = n[k] - rates[k] * (n[k] - neq[k]) + (1.0 - 0.5 * rates[k]) * S[k];
+    for (int i = 0; i < 5; ++i) {
+        ds[i] = 0;
+        for (int k = 0; k < 5; ++k) ds[i] += N5inv[i][k] * ns[k];
+    }
+}
+
+static void collide(const or_params* p, const double f[9], const double g[5], const double h[5],
+                    double hist[4], double fs[9], double gs[5], double hs[5], or_macro* o)
+{
+    macro(p, f, g, h, o);
+    double rho0 = p->rho0, eps = p->eps;
+    double ux = o->ux, uy = o->uy, Fx = o->Fx, Fy = o->Fy, rho = o->rho;
+    /* Eqs. 12-13: m = M f */
+    double m[9];
+    for (int k = 0; k < 9; ++k) {
+        m[k] = 0;
+        for (int i = 0; i < 9; ++i) m[k] += M9[k][i] * f[i];
+    }
+    /* Eq. 14 with alpha_1 = 1, alpha_2 = -3 (Sec. 3.1) */
+    double u2 = ux * ux + uy * uy;
+    double a1 = 1.0, a2 = -3.0;
+    double meq[9] = {rho,
+                     -2.0 * rho + 3.0 * rho0 * u2 / eps,
+                     a1 * rho + a2 * rho0 * u2 / eps,
+                     rho0 * ux,
+                     -rho0 * ux,
+                     rho0 * uy,
+                     -rho0 * uy,
+                     rho0 * (ux * ux - uy * uy) / eps,
+                     rho0 * ux * uy / eps};
+    /* Eq. 15 */
+    double uF = ux * Fx + uy * Fy;
+    double S[9] = {0.0,
+                   6.0 * rho0 * uF / eps,
+                   -6.0 * rho0 * uF / eps,
+                   rho0 * Fx,
+                   -rho0 * Fx,
+                   rho0 * Fy,
+                   -rho0 * Fy,
+                   2.0 * rho0 * (ux * Fx - uy * Fy) / eps,
+                   rho0 * (ux * Fy + uy * Fx) / eps};
+    /* Eq. 10 (delta_t = 1) */
+    double ms[9];
+    for (int k = 0; k < 9; ++k)
+        ms[k] = m[k] - p->s[k] * (m[k] - meq[k]) + (1.0 - 0.5 * p->s[k]) * S[k];
+    /* f* = M^-1 m* */
+    for (int i = 0; i < 9; ++i) {
+        fs[i] = 0;
+        for (int k = 0; k < 9; ++k) fs[i] += M9inv[i][k] * ms[k];
+    }
+    /* Eq. 27 with the explicit difference d(Tu)/dt = (Tu)|t - (Tu)|t-1 (Sec. 3.2) */
+    double Tux = o->T * ux, Tuy = o->T * uy, Cux = o->C * ux, Cuy = o->C * uy;
+    double XTx = Tux - hist[0], XTy = Tuy - hist[1];
+    double XCx = Cux - hist[2], XCy = Cuy - hist[3];
+    hist[0] = Tux; hist[1] = Tuy; hist[2] = Cux; hist[3] = Cuy;
+    collide_d2q5(p, p->zeta, p->sigma, o->T, ux, uy, XTx, XTy, g, gs);   /* Eq. 21, 24 */
+    collide_d2q5(p, p->eta, eps, o->C, ux, uy, XCx, XCy, h, hs);         /* Eq. 22, 25 */
+}
+
+void or_collide_node(const or_params* p, const double f[9], const double g[5],
+                     const double h[5], double hist[4], double fs[9], double gs[5],
+                     double hs[5], double mac[7])
+{
+    ensure_inverses();
+    or_macro o;
+    collide(p, f, g, h, hist, fs, gs, hs, &o);
+    mac[0] = o.rho; mac[1] = o.ux; mac[2] = o.uy; mac[3] = o.T; mac[4] = o.C;
+    mac[5] = o.Fx; mac[6] = o.Fy;
+}
+
+/* ---- creation ---------------------------------------------------------------- */
+
+or_state* or_create(const or_params* p, uint64_t seed, double noise, const double* T_init,
+                    const double* C_init)
+{
+    ensure_inverses();
+    or_state* s = (or_state*)calloc(1, sizeof(or_state));
+    if (!s) return NULL;
+    s->p = *p;
+    s->n = (size_t)p->nx * (size_t)p->ny;
+    size_t n = s->n;
+    s->f = (double*)calloc(9 * n, sizeof(double));
+    s->g = (double*)calloc(5 * n, sizeof(double));
+    s->h = (double*)calloc(5 * n, sizeof(double));
+    s->hist = (double*)calloc(4 * n, sizeof(double));
+    s->f2 = (double*)calloc(9 * n, sizeof(double));
+    s->g2 = (double*)calloc(5 * n, sizeof(double));
+    s->h2 = (double*)calloc(5 * n, sizeof(double));
+    if (!s->f || !s->g || !s->h || !s->hist || !s->f2 || !s->g2 || !s->h2) {
+        or_destroy(s);
+        return NULL;
+    }
+    double varpi = p->varpi;
+    for (int j = 0; j < p->ny; ++j)
+        for (int i = 0; i < p->nx; ++i) {
+            size_t x = (size_t)j * p->nx + i;
+            /* noise key: (field * ny + j) * nx + i, field 0 = T, 1 = C */
+            double T = T_init ? T_init[x]
+                              : p->T0 + noise * (2.0 * or_uniform(seed, x) - 1.0);
+            double C = C_init ? C_init[x]
+                              : p->C0 + noise * (2.0 * or_uniform(seed, n + x) - 1.0);
+            /* Eq. 20 at rho = rho0, u = 0 */
+            for (int q = 0; q < 9; ++q) s->f[q * n + x] = W9[q] * p->rho0;
+            /* Eq. 28 at u = 0 */
+            s->g[x] = p->sigma * T - varpi * T;
+            s->h[x] = p->eps * C - varpi * C;
+            for (int q = 1; q < 5; ++q) {
+                s->g[q * n + x] = varpi / 4 * T;
+                s->h[q * n + x] = varpi / 4 * C;
+            }
+        }
+    /* history = (T u, C u) of the initial state */
+    for (size_t x = 0; x < n; ++x) {
+        double fl[9], gl[5], hl[5];
+        for (int q = 0; q < 9; ++q) fl[q] = s->f[q * n + x];
+        for (int q = 0; q < 5; ++q) { gl[q] = s->g[q * n + x]; hl[q] = s->h[q * n + x]; }
+        or_macro o;
+        macro(&s->p, fl, gl, hl, &o);
+        s->hist[0 * n + x] = o.T * o.ux;
+        s->hist[1 * n + x] = o.T * o.uy;
+        s->hist[2 * n + x] = o.C * o.ux;
+        s->hist[3 * n + x] = o.C * o.uy;
+    }
+    return s;
+}
+
+void or_destroy(or_state* s)
+{
+    if (!s) return;
+    free(s->f); free(s->g); free(s->h); free(s->hist);
+    free(s->f2); free(s->g2); free(s->h2);
+    free(s);
+}
+
+/* ---- one time step ------------------------------------------------------------- */
+
+void or_step(or_state* s, long nsteps)
+{
+    const or_params* p = &s->p;
+    const int nx = p->nx, ny = p->ny;
+    const size_t n = s->n;
+    int opp[9];
+    for (int q = 0; q < 9; ++q) opp[q] = opposite(q);
+    const double wt_axis = p->varpi / 4;  /* w~_1..4 */
+    for (long step = 0; step < nsteps; ++step) {
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                size_t x = (size_t)j * nx + i;
+                double f[9], g[5], h[5], hist[4], fs[9], gs[5], hs[5];
+                for (int q = 0; q < 9; ++q) f[q] = s->f[q * n + x];
+                for (int q = 0; q < 5; ++q) { g[q] = s->g[q * n + x]; h[q] = s->h[q * n + x]; }
+                for (int k = 0; k < 4; ++k) hist[k] = s->hist[k * n + x];
+                or_macro o;
+                collide(p, f, g, h, hist, fs, gs, hs, &o);
+                for (int k = 0; k < 4; ++k) s->hist[k * n + x] = hist[k];
+                /* Eq. 11: push f*_q to x + e_q; links that leave the cavity are
+                 * reflected at the halfway wall back into the opposite slot of x. */
+                for (int q = 0; q < 9; ++q) {
+                    int ti = i + EX[q], tj = j + EY[q];
+                    if (p->periodic_x) ti = (ti + nx) % nx;
+                    if (p->periodic_y) tj = (tj + ny) % ny;
+                    if (ti >= 0 && ti < nx && tj >= 0 && tj < ny)
+                        s->f2[q * n + (size_t)tj * nx + ti] = fs[q];
+                    else
+                        s->f2[opp[q] * n + x] = fs[q];       /* no-slip bounce-back */
+                }
+                for (int q = 0; q < 5; ++q) {
+                    int ti = i + EX[q], tj = j + EY[q];
+                    if (p->periodic_x) ti = (ti + nx) % nx;
+                    if (p->periodic_y) tj = (tj + ny) % ny;
+                    if (ti >= 0 && ti < nx && tj >= 0 && tj < ny) {
+                        s->g2[q * n + (size_t)tj * nx + ti] = gs[q];
+                        s->h2[q * n + (size_t)tj * nx + ti] = hs[q];
+                        continue;
+                    }
+                    int lr = (ti < 0 || ti >= nx);           /* left/right wall link */
+                    int type = lr ? p->scalar_lr : p->scalar_tb;
+                    if (type == OR_DIRICHLET) {
+                        /* anti-bounce-back: g_opp(x) = -g*_q(x) + 2 w~ T_w */
+                        int side = lr ? (ti < 0 ? 0 : 1) : (tj < 0 ? 0 : 1);
+                        s->g2[opp[q] * n + x] = -gs[q] + 2.0 * wt_axis * p->Tw[side];
+                        s->h2[opp[q] * n + x] = -hs[q] + 2.0 * wt_axis * p->Cw[side];
+                    } else {
+                        /* adiabatic / impermeable: plain bounce-back */
+                        s->g2[opp[q] * n + x] = gs[q];
+                        s->h2[opp[q] * n + x] = hs[q];
+                    }
+                }
+            }
+        }
+        double* t;
+        t = s->f; s->f = s->f2; s->f2 = t;
+        t = s->g; s->g = s->g2; s->g2 = t;
+        t = s->h; s->h = s->h2; s->h2 = t;
+        s->t += 1;
+    }
+}
+
+/* ---- read-out ---------------------------------------------------------------- */
+
+void or_fields(const or_state* s, double* ux, double* uy, double* T, double* C, double* rho)
+{
+    size_t n = s->n;
+    for (size_t x = 0; x < n; ++x) {
+        double f[9], g[5], h[5];
+        for (int q = 0; q < 9; ++q) f[q] = s->f[q * n + x];
+        for (int q = 0; q < 5; ++q) { g[q] = s->g[q * n + x]; h[q] = s->h[q * n + x]; }
+        or_macro o;
+        macro(&s->p, f, g, h, &o);
+        if (ux) ux[x] = o.ux;
+        if (uy) uy[x] = o.uy;
+        if (T) T[x] = o.T;
+        if (C) C[x] = o.C;
+        if (rho) rho[x] = o.rho;
+    }
+}
+
+/* Eq. 38 with a second-order one-sided wall gradient through the wall value and
+ * the first two nodes (at distances 1/2 and 3/2 from the halfway wall):
+ *   dPhi/dx|wall = (-8 Phi_w + 9 Phi_0 - Phi_1) / 3  (left), mirrored on the right.
+ * Nu(y) = -L dT/dx / dT with L = nx; the mean is the midpoint rule over the ny rows. */
+void or_nusselt_sherwood(const or_state* s, double out[4])
+{
+    const or_params* p = &s->p;
+    int nx = p->nx, ny = p->ny;
+    size_t n = s->n;
+    double* T = (double*)malloc(n * sizeof(double));
+    double* C = (double*)malloc(n * sizeof(double));
+    or_fields(s, NULL, NULL, T, C, NULL);
+    double dT = p->Tw[0] - p->Tw[1], dC = p->Cw[0] - p->Cw[1];
+    double nuL = 0, shL = 0, nuR = 0, shR = 0;
+    for (int j = 0; j < ny; ++j) {
+        const double* Tr = T + (size_t)j * nx;
+        const double* Cr = C + (size_t)j * nx;
+        double dTdx_L = (-8.0 * p->Tw[0] + 9.0 * Tr[0] - Tr[1]) / 3.0;
+        double dCdx_L = (-8.0 * p->Cw[0] + 9.0 * Cr[0] - Cr[1]) / 3.0;
+        double dTdx_R = (8.0 * p->Tw[1] - 9.0 * Tr[nx - 1] + Tr[nx - 2]) / 3.0;
+        double dCdx_R = (8.0 * p->Cw[1] - 9.0 * Cr[nx - 1] + Cr[nx - 2]) / 3.0;
+        nuL += -nx * dTdx_L / dT;
+        shL += -nx * dCdx_L / dC;
+        nuR += -nx * dTdx_R / dT;
+        shR += -nx * dCdx_R / dC;
+    }
+    out[0] = nuL / ny; out[1] = shL / ny; out[2] = nuR / ny; out[3] = shR / ny;
+    free(T);
+    free(C);
+}
+
+void or_get(const or_state* s, double* f, double* g, double* h, double* hist)
+{
+    size_t n = s->n;
+    if (f) memcpy(f, s->f, 9 * n * sizeof(double));
+    if (g) memcpy(g, s->g, 5 * n * sizeof(double));
+    if (h) memcpy(h, s->h, 5 * n * sizeof(double));
+    if (hist) memcpy(hist, s->hist, 4 * n * sizeof(double));
+}
+
+void or_set(or_state* s, const double* f, const double* g, const double* h, const double* hist)
+{
+    size_t n = s->n;
+    if (f) memcpy(s->f, f, 9 * n * sizeof(double));
+    if (g) memcpy(s->g, g, 5 * n * sizeof(double));
+    if (h) memcpy(s->h, h, 5 * n * sizeof(double));
+    if (hist) memcpy(s->hist, hist, 4 * n * sizeof(double));
+}
+
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int or_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,106 @@
+/*
+ * FP64 CPU oracle for the REV-scale MRT lattice Boltzmann model of
+ * double-diffusive convection in porous media (Liu & He, arXiv:1708.07525).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code is the plain, slow, obviously correct
+ * statement of what one time step computes; it exists so that the CUDA path
+ * can be checked against it.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or constant with the GPU library, and never includes anything from
+ * it.
+ *
+ * What it follows (section / equation of the paper):
+ *   - D2Q9 flow lattice, MRT collision in moment space        Sec. 3.1, Eqs. 8-15
+ *   - density and velocity, explicit velocity closed form      Eqs. 16-19
+ *   - Brinkman-Forchheimer total force and buoyancy            Sec. 2, Eqs. 5-7
+ *   - D2Q5 temperature / concentration MRT collisions with the
+ *     modified equilibrium moments and source terms            Sec. 3.2, Eqs. 21-27
+ *   - streaming in velocity space                              Eq. 11
+ *   - Nusselt / Sherwood numbers                               Sec. 4.1, Eq. 38
+ *   - parameter mapping from Ra, Pr, Le, Da, Ma                Sec. 4 and 4.1
+ * Readings where the paper is silent (all stated again beside the code):
+ *   - walls: no-slip halfway bounce-back for f; anti-bounce-back (Dirichlet)
+ *     and bounce-back (adiabatic) for g, h.  The paper itself uses
+ *     non-equilibrium extrapolation (Sec. 3.3); the cavity workloads specify
+ *     halfway walls.
+ *   - the time derivative of T*u in Eq. 27 is the explicit backward
+ *     difference the paper suggests (Sec. 3.2), with the history initialised
+ *     to T*u of the initial state, so the source vanishes at the first step.
+ *   - initial noise: SplitMix64 (Steele, Lea & Flood 2014), see or_noise().
+ *
+ * Parity status: every function here is pinned by tests under tests/
+ * (identities between the paper's moment- and velocity-space forms,
+ * conservation, exact conduction profile, Brinkman channel, Table 1).
+ */
+#ifndef LBM_ORACLE_H
+#define LBM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_DIRICHLET = 0, OR_ADIABATIC = 1 };
+
+typedef struct {
+    /* grid (nodes); walls sit half a spacing outside the outermost nodes */
+    int nx, ny;
+    /* physical inputs (Sec. 2, dimensionless groups) */
+    double Ra, Da, eps, Pr, Le, N, J, sigma, Ma, varpi;
+    /* derived lattice quantities (filled by or_derive, may be edited by tests) */
+    double rho0, cs2, U, nu, nu_e, alpha_e, D_e, csT2, K, Feps, gbT, gbC, T0, C0;
+    double s[9];      /* Lambda = diag(s_rho, s_e, s_eps, s_j, s_q, s_j, s_q, s_nu, s_nu) */
+    double zeta[5];   /* Theta  = diag(zeta_0, zeta_a, zeta_a, zeta_e, zeta_eps) */
+    double eta[5];    /* Q      = diag(eta_0, eta_D, eta_D, eta_e, eta_eps) */
+    /* boundary and test knobs */
+    int periodic_x, periodic_y;
+    int scalar_lr, scalar_tb;   /* OR_DIRICHLET / OR_ADIABATIC for g and h */
+    double Tw[2], Cw[2];        /* Dirichlet values, [0]=left (x=0), [1]=right (x=nx) */
+    double Gx;                  /* constant external body force along x (enters as eps*G) */
+} or_params;
+
+typedef struct or_state or_state;
+
+/* Fill the derived fields of p from nx, Ra, Da, eps, Pr, Le, N, J, sigma, Ma, varpi.
+ * Returns 0 on success, nonzero if a relaxation rate leaves (0,2) or an input is invalid. */
+int or_derive(or_params* p);
+
+/* Create a state at t = 0: f = f_eq(rho0, u=0), g = g_eq(T, 0), h = h_eq(C, 0), where
+ * T = T0 + noise*(2U-1), C = C0 + noise*(2U'-1) from SplitMix64(seed), unless T_init /
+ * C_init (row-major [ny][nx]) are given.  History = (T u, C u) at t = 0. */
+or_state* or_create(const or_params* p, uint64_t seed, double noise,
+                    const double* T_init, const double* C_init);
+void or_destroy(or_state* s);
+
+/* n time steps: collide (Eqs. 10, 21, 22), stream (Eq. 11), wall rules. */
+void or_step(or_state* s, long n);
+long or_time(const or_state* s);
+
+/* Macroscopic fields at the current time level (pre-collision), row-major [ny][nx].
+ * Any pointer may be NULL. u is from Eq. 18, T and C from Eq. 26, rho from Eq. 16. */
+void or_fields(const or_state* s, double* ux, double* uy, double* T, double* C, double* rho);
+
+/* Mean Nu and Sh on the left and right walls (Eq. 38), out = {Nu_L, Sh_L, Nu_R, Sh_R}. */
+void or_nusselt_sherwood(const or_state* s, double out[4]);
+
+/* Copy the distributions out / in, layout [q][ny][nx]; hist is [4][ny][nx] =
+ * (T u_x, T u_y, C u_x, C u_y) at the previous collision. */
+void or_get(const or_state* s, double* f, double* g, double* h, double* hist);
+void or_set(or_state* s, const double* f, const double* g, const double* h, const double* hist);
+
+/* One node's collision, for brute-force checks.  hist is read and updated.
+ * mac = {rho, ux, uy, T, C, Fx, Fy}. */
+void or_collide_node(const or_params* p, const double f[9], const double g[5],
+                     const double h[5], double hist[4], double fs[9], double gs[5],
+                     double hs[5], double mac[7]);
+
+/* The k-th SplitMix64 output of a generator seeded with `seed`, as a double in [0,1). */
+double or_uniform(uint64_t seed, uint64_t k);
+
+void or_set_threads(int n);
+int or_get_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
