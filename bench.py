@@ -1,0 +1,350 @@
+"""Benchmark of the fused three-lattice MRT-LB step on GB300.
+
+One bench step = one pass of the whole hot path over the cavity: 100 time
+steps of the fused collide-stream kernel (pull streaming with wall rules,
+macroscopic fields, porous force, D2Q9 + 2 x D2Q5 MRT collisions) plus the
+FP64 Nu/Sh wall reduction and the steady-state residual.  Workload: the
+4096 x 4096 opposing-buoyancy porous cavity (Ra = 1e5, Da = 1e-3, eps = 0.4,
+Pr = 1, Le = 5, N = -1) in FP32 shifted storage, two-buffer pull layout.
+The state (2.8 GB) is far larger than L2 (129 MB), so no flush is needed.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3-lattice GLUPS & %HBM peak; served solves/s, p99 vs plain at Nu/Sh err≤1e-3"
+STEPS_PER_BENCH_STEP = 100
+# algorithmic bytes per node update: 19 distributions + 4 history values, read and written
+BYTES_PER_NODE = {"f64": 2 * (19 * 8 + 4 * 8), "f32": 2 * (19 * 4 + 4 * 4),
+                  "bf16": 2 * (19 * 2 + 4 * 4), "f16": 2 * (19 * 2 + 4 * 4)}
+BYTES_PER_NODE_19 = {"f64": 2 * 19 * 8, "f32": 2 * 19 * 4, "bf16": 2 * 19 * 2, "f16": 2 * 19 * 2}
+KERNEL_SOURCES = ["paper_1708_07525_gb300/csrc/lbm_kernels.cuh",
+                  "paper_1708_07525_gb300/csrc/lbm_device.cuh",
+                  "paper_1708_07525_gb300/csrc/lbm_launchers.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        e = d.get(name)
+        if e and e.get("kernel_hash") == kernel_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(nx, ny, spec, budget_s=12.0):
+    """The FP64 oracle as it stands, all host cores, on the same cavity for as many
+    whole time steps as fit in about `budget_s` seconds (at least one)."""
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    p = O.derive(*spec.args())
+    o = O.Oracle(p, seed=spec.seed, noise=spec.noise)
+    t0 = time.perf_counter()
+    o.step(1)
+    dt1 = time.perf_counter() - t0
+    more = max(0, int(budget_s / max(dt1, 1e-9)) - 1)
+    more = min(more, 50)
+    t0 = time.perf_counter()
+    if more:
+        o.step(more)
+    dt = time.perf_counter() - t0
+    steps, secs = (more, dt) if more else (1, dt1)
+    glups = nx * ny * steps / secs / 1e9
+    return {"value": glups, "unit": "GLUPS", "cores": O.get_threads(), "kind": "oracle",
+            "sample": f"{nx}x{ny} cavity, {steps} time step(s) of the FP64 oracle after 1 warm-up "
+                      f"step, {secs:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    from paper_1708_07525_gb300.workloads import throughput_cavity
+    from oracle import oracle as O
+    n = args.size
+    spec = throughput_cavity(n)
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    o = O.Oracle(O.derive(*spec.args()), seed=spec.seed, noise=spec.noise)
+    per_step = max(1, int(args.ref_steps))
+    for _ in range(args.warmup):
+        o.step(per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(per_step)
+    secs = time.perf_counter() - t0
+    value = n * n * per_step * args.steps / secs / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"porous cavity {n}x{n}, Ra=1e5 Da=1e-3 eps=0.4 Pr=1 Le=5 N=-1",
+                   "nx": n, "ny": n, "bench_step": f"{per_step} time step(s) of the CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": O.get_threads(), "kind": "oracle",
+                         "sample": f"{n}x{n} cavity, {per_step} time step(s) per bench step"},
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_setup(args.gpus)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_1708_07525_gb300 import lbm
+    from paper_1708_07525_gb300.workloads import throughput_cavity
+
+    n = args.size
+    spec = throughput_cavity(n)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    cav = lbm.Cavity(*spec.args(), precision=args.precision, layout=args.layout,
+                     seed=spec.seed + rank, noise=spec.noise, stream=stream.cuda_stream,
+                     block=(args.bx, args.by))
+    k = STEPS_PER_BENCH_STEP
+
+    def bench_step(ev_pair=None):
+        if ev_pair is not None:
+            ev_pair[0].record(stream)
+        cav.step(k)
+        if ev_pair is not None:
+            ev_pair[1].record(stream)
+        nush = cav.nusselt_sherwood()
+        r = cav.residual()
+        return nush, r
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(dev) as clk:
+        start.record(stream)
+        for s in range(args.steps):
+            nush, r = bench_step(evs[s])
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    total_ms = start.elapsed_time(stop)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in evs) / (args.steps * k)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    nodes = n * n
+    value = world * nodes * k * args.steps / (total_ms / 1e3) / 1e9
+
+    # end to end through the public API with host buffers: each step re-initialises the
+    # cavity from pinned host T/C fields (H2D), runs the 100 time steps, and reads the
+    # Nu/Sh result back (D2H).
+    Th = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    Ch = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    rng = np.random.default_rng(10 + rank)
+    Th.numpy()[:] = 0.5 + spec.noise * rng.uniform(-1, 1, (n, n))
+    Ch.numpy()[:] = 0.5 + spec.noise * rng.uniform(-1, 1, (n, n))
+
+    def e2e_step():
+        cav.reset(T_ptr=Th.data_ptr(), C_ptr=Ch.data_ptr())
+        cav.step(k)
+        return cav.nusselt_sherwood()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * nodes * k * args.steps / e2e_s / 1e9
+
+    peak, peak_kind = measured_peaks()
+    bpn = BYTES_PER_NODE[args.precision]
+    achieved = nodes * bpn / (kernel_ms / 1e3) / 1e9
+    kname = f"step_{args.layout}_{args.precision}_{n}"
+    traffic = profiled_traffic(kname)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {
+            "workload": f"porous cavity {n}x{n}, Ra=1e5 Da=1e-3 eps=0.4 Pr=1 Le=5 N=-1, "
+                        f"{args.precision} {'two-buffer pull' if args.layout == 'ab' else 'in-place AA'}",
+            "nx": n, "ny": n, "time_steps_per_bench_step": k,
+            "bench_step": f"{k} fused time steps + FP64 Nu/Sh reduction + residual",
+            "l2": "state larger than L2 (no flush needed)" if nodes * bpn / 2 > 129e6
+                  else "state fits in L2 (cache-resident figure)",
+            "parallelism": f"replicas x{world}",
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": f"step_{args.layout}_kernel<{args.precision}>",
+                     "kernel_us_per_launch": kernel_ms * 1e3,
+                     "algorithmic_bytes_per_node": bpn,
+                     "frac_19_distribution_convention":
+                         nodes * BYTES_PER_NODE_19[args.precision] / (kernel_ms / 1e3) / 1e9 / peak},
+        "e2e": {"value": e2e_value, "unit": "GLUPS",
+                "h2d_bytes_per_step": 2 * nodes * 8, "d2h_bytes_per_step": 4 * 8},
+        "gpu_launches": args.steps * (k + 1 + 2),
+        "clocks": clk.summary(),
+        "nusselt_sherwood": [float(x) for x in nush],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n, n, spec, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    cav.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16", "f16"])
+    ap.add_argument("--layout", default="ab", choices=["ab", "aa"])
+    ap.add_argument("--bx", type=int, default=0)
+    ap.add_argument("--by", type=int, default=0)
+    ap.add_argument("--ref-steps", type=int, default=1)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,200 @@
+/*
+ * liblbm -- C ABI of the GB300 (sm_103a) implementation of the REV-scale
+ * multiple-relaxation-time lattice Boltzmann model for double-diffusive
+ * convection in fluid-saturated porous media (Liu & He, arXiv:1708.07525).
+ *
+ * One cavity ("context") holds three lattices on the device:
+ *   f  D2Q9 flow distributions           (Sec. 3.1, Eqs. 8-20)
+ *   g  D2Q5 temperature distributions    (Sec. 3.2, Eqs. 21, 23, 24, 26-28)
+ *   h  D2Q5 concentration distributions  (Sec. 3.2, Eqs. 22, 23, 25-28)
+ * plus four history values per node (T u, C u at the previous step) for the
+ * explicit time derivative in the source terms of Eq. 27.
+ *
+ * One time step = one fused kernel launch: pull-streaming (Eq. 11) with the
+ * halfway wall rules, macroscopic fields (Eqs. 16, 18-19, 26), total force
+ * (Eqs. 5-6), the D2Q9 collision in moment space (Eq. 10 with Eqs. 12-15) and
+ * the two D2Q5 collisions (Eqs. 21-22 with Eqs. 24-25, 27).
+ *
+ * Cavity: nodes (i, j), 0 <= i < nx, 0 <= j < ny, at positions (i+1/2, j+1/2);
+ * walls at x = 0, x = nx, y = 0, y = ny, halfway between the outermost nodes
+ * and their missing neighbours.  Left wall T = C = 1, right wall T = C = 0,
+ * top and bottom adiabatic and impermeable, all walls no-slip.  The paper's
+ * own walls are node-based non-equilibrium extrapolation (Sec. 3.3); this
+ * library implements halfway bounce-back (f), anti-bounce-back (Dirichlet g,
+ * h) and bounce-back (adiabatic g, h).
+ *
+ * Conventions for every entry point:
+ *   - Returns an lbm_status; never aborts, exits or traps.  The message of the
+ *     last failure is available from lbm_last_error().
+ *   - Host arrays are caller-owned, row-major [ny][nx] doubles unless stated.
+ *   - Device memory is owned by the library (through the caller's allocator
+ *     hooks when given) and released by lbm_destroy().
+ *   - Work is enqueued on the context's stream; calls that return host data
+ *     synchronise that stream.
+ *   - A context must not be used from two host threads at once.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID = 1,      /* bad argument or parameter set */
+    LBM_ERR_NOMEM = 2,        /* device or host allocation failed */
+    LBM_ERR_CUDA = 3,         /* a CUDA runtime call failed; see lbm_last_error() */
+    LBM_ERR_DIVERGED = 4,     /* NaN / Inf found by a reduction */
+    LBM_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    LBM_ERR_UNCONVERGED = 6   /* step cap reached before the residual tolerance */
+} lbm_status;
+
+/* Storage precision of the 19 distributions.  F64 computes in FP64; the
+ * others compute in FP32.  All store deviations from the rest equilibria
+ * f_i - f_i^eq(rho0, 0), g_i - g_i^eq(T0, 0), h_i - h_i^eq(C0, 0) (Eqs. 20, 28). */
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_BF16 = 2, LBM_F16 = 3 };
+/* Memory pattern: two buffers with pull streaming, or one buffer in place (AA). */
+enum { LBM_AB_PULL = 0, LBM_AA = 1 };
+/* Wall type of the scalar fields g, h on a pair of walls. */
+enum { LBM_WALL_DIRICHLET = 0, LBM_WALL_ADIABATIC = 1 };
+
+typedef struct {
+    int nx, ny;                 /* lattice nodes; both >= 3 */
+} lbm_grid;
+
+/* Device allocator hooks: alloc(bytes, user, stream) returns a device pointer
+ * aligned to at least 256 bytes, or NULL; free(ptr, user, stream). */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* user, void* stream);
+typedef void (*lbm_free_fn)(void* ptr, void* user, void* stream);
+
+/* Options; a zero-initialised struct (or NULL) selects the paper's defaults. */
+typedef struct {
+    int precision;              /* LBM_F64 (default) | LBM_F32 | LBM_BF16 | LBM_F16 */
+    int layout;                 /* LBM_AB_PULL (default) | LBM_AA */
+    double Ma;                  /* Mach number U / c_s, 0 -> 0.1 (Sec. 4.1) */
+    double varpi;               /* D2Q5 weight parameter, 0 -> 2/5 (Sec. 4) */
+    uint64_t seed;              /* initial-noise seed (SplitMix64) */
+    double noise;               /* amplitude of the uniform initial noise on T and C;
+                                   negative -> 0, zero -> default 1e-3 */
+    const double* T_init;       /* optional host [ny][nx] initial T (overrides noise) */
+    const double* C_init;       /* optional host [ny][nx] initial C */
+    void* stream;               /* cudaStream_t; NULL -> the library creates its own */
+    lbm_alloc_fn alloc;         /* NULL -> cudaMalloc / cudaFree */
+    lbm_free_fn free;
+    void* alloc_user;
+    int block_x, block_y;       /* launch tile of the step kernel; 0 -> tuned default */
+    int graph_chunk;            /* steps per captured CUDA graph; 0 -> default, <0 -> off */
+} lbm_options;
+
+/* Derived lattice constants (Sec. 4 / 4.1 mapping).  Filled by
+ * lbm_derive_params() from the dimensionless groups, or by the caller for
+ * lbm_create_raw().  Units: lattice (delta_x = delta_t = 1, rho0 = 1). */
+typedef struct {
+    int nx, ny;
+    double eps;                 /* porosity phi of Eqs. 2-5 */
+    double sigma;               /* heat capacity ratio of Eq. 3 */
+    double varpi;               /* D2Q5 model parameter (Eq. 24), c_sT^2 = varpi / 2 */
+    double nu;                  /* fluid viscosity in the Darcy term of Eq. 5 */
+    double K;                   /* permeability, K = Da L^2 */
+    double Feps;                /* Forchheimer coefficient, Eq. 7 */
+    double gbT, gbC;            /* g beta_T dT and g beta_C dC of Eq. 6 */
+    double Gx;                  /* extra constant body force along x (0 for cavities) */
+    double T0, C0;              /* reference values of Eq. 6 and of the storage shift */
+    double s[9];                /* Lambda of Eq. 9 */
+    double zeta[5];             /* Theta of Eq. 21 */
+    double eta[5];              /* Q of Eq. 22 */
+    double Tw[4], Cw[4];        /* Dirichlet wall values by side: [0] left (x = 0),
+                                   [1] right (x = nx), [2] bottom (y = 0), [3] top (y = ny) */
+    int wall_lr, wall_tb;       /* LBM_WALL_* for g and h on left/right, bottom/top */
+} lbm_params;
+
+/* Parameter mapping of Sec. 4 and 4.1 (L = nx, c_s^2 = 1/3, U = Ma c_s,
+ * nu_e = J U L sqrt(Pr / Ra), alpha_e = nu / Pr, D_e = alpha_e / Le,
+ * s_nu, zeta_a, eta_D from Eq. 29 and the nu_e relation of Sec. 3.1,
+ * g beta_T = U^2 / L, g beta_C = N g beta_T, K = Da L^2, F_eps of Eq. 7,
+ * fixed rates of Sec. 4).  Ma <= 0 -> 0.1, varpi <= 0 -> 0.4.
+ * Returns LBM_ERR_INVALID if nx or ny < 3, eps is outside (0, 1], Da, Ra, Pr,
+ * Le, J or sigma is not positive, or a relaxation rate leaves (0, 2). */
+lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, double Pr,
+                             double Le, double N, double J, double sigma, double Ma,
+                             double varpi, lbm_params* out);
+
+/* Create a cavity at t = 0: u = 0, rho = rho0, T = C = 1/2 plus uniform noise
+ * of amplitude opt->noise drawn by SplitMix64 (Steele, Lea & Flood 2014) with
+ * key (field * ny + j) * nx + i (field 0 = T, 1 = C), f = f^eq (Eq. 20),
+ * g, h = equilibria of Eq. 28, history = (T u, C u) of that state, so the
+ * source of Eq. 27 vanishes at the first step.  On success *out owns the
+ * device state.  Errors: LBM_ERR_INVALID (see lbm_derive_params, or out is
+ * NULL), LBM_ERR_NOMEM, LBM_ERR_CUDA. */
+lbm_status lbm_create(lbm_grid grid, double Ra, double Da, double eps, double Pr, double Le,
+                      double N, double J, double sigma, const lbm_options* opt,
+                      lbm_ctx** out);
+
+/* Same, from explicit lattice constants (used for analytic test cases). */
+lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_ctx** out);
+
+/* Re-initialise the cavity at t = 0 as lbm_create does, from caller-owned host
+ * [ny][nx] initial fields T_init and C_init (both or neither; pinned host memory
+ * makes the copy faster), or from the SplitMix64 noise with the given seed and
+ * amplitude (noise < 0 -> none, 0 -> 1e-3).  The first call with fields
+ * allocates a device staging buffer of 16 nx ny bytes, kept until destroy.
+ * Asynchronous on the context's stream; the host arrays must stay valid until
+ * the stream has passed this point. */
+lbm_status lbm_reset(lbm_ctx* ctx, const double* T_init, const double* C_init, uint64_t seed,
+                     double noise);
+
+/* Advance n >= 0 time steps (asynchronous on the context's stream). */
+lbm_status lbm_step(lbm_ctx* ctx, int64_t n);
+
+/* Number of time steps taken since creation (or since the loaded checkpoint). */
+int64_t lbm_time(const lbm_ctx* ctx);
+
+/* Macroscopic fields at the current time level, before collision:
+ * u from Eq. 18, T and C from Eq. 26, rho from Eq. 16.  Caller-owned host
+ * arrays [ny][nx]; any pointer may be NULL.  Synchronises the stream. */
+lbm_status lbm_fields(lbm_ctx* ctx, double* ux, double* uy, double* T, double* C,
+                      double* rho);
+
+/* Mean Nusselt and Sherwood numbers on the left and right walls (Eq. 38),
+ * out = {Nu_L, Sh_L, Nu_R, Sh_R}, reduced in FP64.  The wall gradient is the
+ * second-order one-sided difference through the wall value and the two
+ * nearest nodes, (-8 T_w + 9 T_0 - T_1) / 3 on the left, mirrored on the
+ * right; Nu(y) = -L dT/dx / dT with L = nx; the mean is over the ny rows.
+ * Synchronises the stream.  LBM_ERR_DIVERGED if a result is not finite. */
+lbm_status lbm_nusselt_sherwood(lbm_ctx* ctx, double out[4]);
+
+/* Steady-state residual: r = max over phi in {u_x, u_y, T, C} of
+ * max|phi_now - phi_snap| / max|phi_now|, where phi_snap is the snapshot of
+ * the previous call (r = +inf on the first call); the snapshot is then
+ * replaced by phi_now.  Reduced in FP64.  Synchronises the stream.
+ * LBM_ERR_DIVERGED if a field value is not finite. */
+lbm_status lbm_residual(lbm_ctx* ctx, double* r);
+
+/* Checkpoint of the full state (distributions, history, time, parameters).
+ * lbm_save with buf == NULL stores the size needed in *len.  lbm_load
+ * requires a checkpoint of a context with the same grid, precision and
+ * layout.  Both synchronise the stream. */
+lbm_status lbm_save(lbm_ctx* ctx, void* buf, size_t* len);
+lbm_status lbm_load(lbm_ctx* ctx, const void* buf, size_t len);
+
+/* Parameters in use, and bytes of device memory the context holds. */
+lbm_status lbm_get_params(const lbm_ctx* ctx, lbm_params* out);
+size_t lbm_device_bytes(const lbm_ctx* ctx);
+
+/* Releases everything the context owns.  NULL is ignored. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last failure on ctx, or of the calling thread's last
+ * failed call that had no context (ctx == NULL).  Never NULL. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,717 @@
+// C ABI of liblbm (declared in include/lbm.h): context management, parameter
+// mapping, stepping with CUDA-graph replay, read-outs, checkpoints.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_launch.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_last_error = "";
+
+void set_global_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+size_t storage_size(int prec) {
+    switch (prec) {
+        case LBM_F64: return 8;
+        case LBM_F32: return 4;
+        default: return 2;
+    }
+}
+
+template <typename R>
+Coef<R> make_coef(const lbm_params& P) {
+    Coef<R> c;
+    std::memset(&c, 0, sizeof c);
+    const double eps = P.eps;
+    c.T0 = (R)P.T0;
+    c.C0 = (R)P.C0;
+    c.inv_sigma = (R)(1.0 / P.sigma);
+    c.inv_eps = (R)(1.0 / eps);
+    c.eps = (R)eps;
+    c.half_eps = (R)(0.5 * eps);
+    c.inv_eps_f = (R)(1.0 / eps);
+    c.gbT = (R)P.gbT;
+    c.gbC = (R)P.gbC;
+    c.Gx = (R)P.Gx;
+    // Eq. 19 with delta_t = 1
+    const double l0 = 0.5 * (1.0 + eps * 0.5 * P.nu / P.K);
+    const double l1 = eps * 0.5 * P.Feps / std::sqrt(P.K);
+    c.l0 = (R)l0;
+    c.l0sq = (R)(l0 * l0);
+    c.l1 = (R)l1;
+    c.drag_lin = (R)(eps * P.nu / P.K);                     // Eq. 5
+    c.drag_quad = (R)(eps * P.Feps / std::sqrt(P.K));
+    c.s1 = (R)P.s[1]; c.s2 = (R)P.s[2]; c.s3 = (R)P.s[3]; c.s4 = (R)P.s[4];
+    c.s5 = (R)P.s[5]; c.s6 = (R)P.s[6]; c.s7 = (R)P.s[7]; c.s8 = (R)P.s[8];
+    c.za1 = (R)P.zeta[1]; c.za2 = (R)P.zeta[2]; c.za3 = (R)P.zeta[3]; c.za4 = (R)P.zeta[4];
+    c.ed1 = (R)P.eta[1]; c.ed2 = (R)P.eta[2]; c.ed3 = (R)P.eta[3]; c.ed4 = (R)P.eta[4];
+    c.c3T = (R)(5.0 * P.varpi - 4.0 * P.sigma);             // Eq. 24
+    c.c3C = (R)(5.0 * P.varpi - 4.0 * eps);                 // Eq. 25
+    const double w = 0.25 * P.varpi;                        // w~_1..4 (Sec. 3.2)
+    for (int s = 0; s < 4; ++s) {
+        c.wallT[s] = (R)(2.0 * w * (P.Tw[s] - P.T0));
+        c.wallC[s] = (R)(2.0 * w * (P.Cw[s] - P.C0));
+    }
+    c.dirichlet_mask = (P.wall_lr == LBM_WALL_DIRICHLET ? 3 : 0) |
+                       (P.wall_tb == LBM_WALL_DIRICHLET ? 12 : 0);
+    return c;
+}
+
+bool rate_ok(double s) { return s > 0.0 && s < 2.0; }
+
+const char* check_params(const lbm_params& P) {
+    if (P.nx < 3 || P.ny < 3) return "nx and ny must be >= 3";
+    if (!(P.eps > 0.0 && P.eps <= 1.0)) return "porosity eps must lie in (0, 1]";
+    if (!(P.sigma > 0.0)) return "sigma must be positive";
+    if (!(P.varpi > 0.0 && P.varpi < 1.0)) return "varpi must lie in (0, 1)";
+    if (!(P.K > 0.0)) return "permeability K must be positive";
+    if (!(P.nu >= 0.0) || !(P.Feps >= 0.0)) return "nu and F_eps must be non-negative";
+    for (int k = 0; k < 9; ++k)
+        if (!rate_ok(P.s[k])) return "a flow relaxation rate lies outside (0, 2)";
+    for (int k = 0; k < 5; ++k)
+        if (!rate_ok(P.zeta[k]) || !rate_ok(P.eta[k]))
+            return "a scalar relaxation rate lies outside (0, 2)";
+    if (P.wall_lr != LBM_WALL_DIRICHLET && P.wall_lr != LBM_WALL_ADIABATIC) return "bad wall_lr";
+    if (P.wall_tb != LBM_WALL_DIRICHLET && P.wall_tb != LBM_WALL_ADIABATIC) return "bad wall_tb";
+    if ((double)P.nx * (double)P.ny > 4.0e9) return "grid too large";
+    return nullptr;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_params P;
+    int prec = LBM_F64, layout = LBM_AB_PULL;
+    Geom G{};
+    size_t esz = 8, rsz = 8;
+    void* buf[2] = {nullptr, nullptr};
+    void* hist = nullptr;
+    double* d_out = nullptr;        // 16 doubles: Nu/Sh and residual results
+    double* d_fields = nullptr;     // lazily allocated [5][ny][nx]
+    double* d_snap = nullptr;       // lazily allocated [4][ny][nx]
+    double* d_partial = nullptr;    // lazily allocated residual partials
+    double* d_stage = nullptr;      // lazily allocated [2][ny][nx] initial-field staging
+    bool snap_valid = false;
+    int cur = 0;                    // two-buffer layout: buffer holding the state
+    int64_t t = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    Coef<double> cd{};
+    Coef<float> cf{};
+    LaunchCfg L{};
+    int graph_chunk = 0;
+    cudaGraphExec_t graph = nullptr;
+    lbm_alloc_fn alloc = nullptr;
+    lbm_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    size_t bytes = 0;
+    std::string err;
+
+    lbm_status fail(lbm_status s, const char* fmt, ...) {
+        char b[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b, sizeof b, fmt, ap);
+        va_end(ap);
+        err = b;
+        g_last_error = b;
+        return s;
+    }
+    lbm_status cuda_fail(cudaError_t e, const char* where) {
+        return fail(LBM_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+    }
+
+    void* dalloc(size_t n) {
+        void* p = nullptr;
+        if (alloc) {
+            p = alloc(n, alloc_user, (void*)stream);
+            if (p && ((uintptr_t)p & 255u)) {   // the kernels assume 256-byte alignment
+                free_fn(p, alloc_user, (void*)stream);
+                p = nullptr;
+            }
+        } else if (cudaMalloc(&p, n) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (p) bytes += n;
+        return p;
+    }
+    void dfree(void* p, size_t n) {
+        if (!p) return;
+        if (alloc)
+            free_fn(p, alloc_user, (void*)stream);
+        else
+            cudaFree(p);
+        bytes -= n;
+    }
+
+    size_t state_bytes() const { return (size_t)NQ * G.plane * esz; }
+    size_t hist_bytes() const { return (size_t)4 * G.plane * rsz; }
+    size_t nodes() const { return (size_t)G.nx * G.ny; }
+    int read_mode() const {
+        if (layout == LBM_AB_PULL) return GATHER_PULL_AB;
+        return (t & 1) ? GATHER_PULL_AA : GATHER_LOCAL;
+    }
+};
+
+namespace {
+
+inline const Coef<double>& coef_of(const lbm_ctx* c, double*) { return c->cd; }
+inline const Coef<float>& coef_of(const lbm_ctx* c, float*) { return c->cf; }
+
+template <typename S>
+cudaError_t dispatch_step(lbm_ctx* c) {
+    using R = typename Real<S>::type;
+    const Coef<R>& k = coef_of(c, (R*)nullptr);
+    if (c->layout == LBM_AB_PULL) {
+        cudaError_t e = launch_step_ab<S>(c->buf[c->cur], c->buf[c->cur ^ 1], c->hist, c->G, k, c->L);
+        c->cur ^= 1;
+        return e;
+    }
+    return launch_step_aa<S>(c->buf[0], c->hist, c->G, k, (c->t & 1) != 0, c->L);
+}
+
+cudaError_t one_step(lbm_ctx* c) {
+    cudaError_t e;
+    switch (c->prec) {
+        case LBM_F64: e = dispatch_step<double>(c); break;
+        case LBM_F32: e = dispatch_step<float>(c); break;
+        case LBM_BF16: e = dispatch_step<__nv_bfloat16>(c); break;
+        default: e = dispatch_step<__half>(c); break;
+    }
+    c->t += 1;
+    return e;
+}
+
+#define LBM_DISPATCH(c, CALL_D, CALL_F, CALL_B, CALL_H) \
+    ((c)->prec == LBM_F64 ? (CALL_D) : (c)->prec == LBM_F32 ? (CALL_F) : (c)->prec == LBM_BF16 ? (CALL_B) : (CALL_H))
+
+cudaError_t run_init(lbm_ctx* c, const InitSpec& I) {
+    const bool pull = c->layout == LBM_AB_PULL;
+    return LBM_DISPATCH(c, launch_init<double>(c->buf[0], c->hist, c->G, c->cd, I, pull, c->stream),
+                        launch_init<float>(c->buf[0], c->hist, c->G, c->cf, I, pull, c->stream),
+                        launch_init<__nv_bfloat16>(c->buf[0], c->hist, c->G, c->cf, I, pull, c->stream),
+                        launch_init<__half>(c->buf[0], c->hist, c->G, c->cf, I, pull, c->stream));
+}
+
+const void* cur_buf(const lbm_ctx* c) { return c->layout == LBM_AB_PULL ? c->buf[c->cur] : c->buf[0]; }
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// (Re)initialise the state at t = 0 from host T / C fields or from the noise.
+lbm_status do_init(lbm_ctx* c, const double* T_host, const double* C_host, uint64_t seed,
+                   double noise) {
+    InitSpec I;
+    std::memset(&I, 0, sizeof I);
+    I.seed = seed;
+    I.noise = noise < 0 ? 0.0 : (noise == 0 ? 1e-3 : noise);
+    I.T0 = c->P.T0;
+    I.C0 = c->P.C0;
+    I.sigma = c->P.sigma;
+    I.eps = c->P.eps;
+    I.varpi = c->P.varpi;
+    const size_t n = c->nodes();
+    cudaError_t e = cudaSuccess;
+    if (T_host) {
+        if (!c->d_stage) {
+            c->d_stage = (double*)c->dalloc(2 * n * sizeof(double));
+            if (!c->d_stage) return c->fail(LBM_ERR_NOMEM, "no device memory for initial fields");
+        }
+        e = cudaMemcpyAsync(c->d_stage, T_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->d_stage + n, C_host, n * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream);
+        I.T_init = c->d_stage;
+        I.C_init = c->d_stage + n;
+    }
+    if (e == cudaSuccess) e = run_init(c, I);
+    if (e != cudaSuccess) return c->cuda_fail(e, "init");
+    c->t = 0;
+    c->cur = 0;
+    c->snap_valid = false;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, double Pr,
+                             double Le, double N, double J, double sigma, double Ma,
+                             double varpi, lbm_params* out) {
+    if (!out) {
+        set_global_error("lbm_derive_params: out is NULL");
+        return LBM_ERR_INVALID;
+    }
+    if (grid.nx < 3 || grid.ny < 3) {
+        set_global_error("lbm_derive_params: nx and ny must be >= 3 (got %d x %d)", grid.nx, grid.ny);
+        return LBM_ERR_INVALID;
+    }
+    if (!(eps > 0.0 && eps <= 1.0) || !(Da > 0.0) || !(Ra > 0.0) || !(Pr > 0.0) || !(Le > 0.0) ||
+        !(J > 0.0) || !(sigma > 0.0) || !std::isfinite(N)) {
+        set_global_error("lbm_derive_params: need eps in (0,1], Da, Ra, Pr, Le, J, sigma > 0");
+        return LBM_ERR_INVALID;
+    }
+    if (!(Ma > 0.0)) Ma = 0.1;
+    if (!(varpi > 0.0)) varpi = 0.4;
+    lbm_params P;
+    std::memset(&P, 0, sizeof P);
+    P.nx = grid.nx;
+    P.ny = grid.ny;
+    const double L = grid.nx;                       // characteristic length = N_x (Sec. 4.1)
+    const double cs2 = 1.0 / 3.0, cs = std::sqrt(cs2);
+    const double U = Ma * cs;                       // Ma = U / c_s
+    const double nu_e = J * U * L * std::sqrt(Pr / Ra);
+    const double nu = nu_e / J;
+    const double alpha_e = nu / Pr;
+    const double D_e = alpha_e / Le;
+    const double csT2 = 0.5 * varpi;
+    const double s_nu = 1.0 / (0.5 + nu_e / cs2);   // nu_e = c_s^2 (1/s_nu - 1/2)
+    const double za = 1.0 / (0.5 + alpha_e / csT2); // Eq. 29
+    const double eD = 1.0 / (0.5 + D_e / csT2);
+    P.eps = eps;
+    P.sigma = sigma;
+    P.varpi = varpi;
+    P.nu = nu;
+    P.K = Da * L * L;                               // Da = K / L^2
+    P.Feps = 1.75 / std::sqrt(150.0 * eps * eps * eps);   // Eq. 7
+    P.gbT = U * U / L;                              // U^2 = g beta_T dT L with dT = 1
+    P.gbC = N * P.gbT;                              // N = beta_C dC / (beta_T dT)
+    P.Gx = 0.0;
+    P.T0 = 0.5;
+    P.C0 = 0.5;
+    const double s[9] = {1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2, s_nu, s_nu};   // Sec. 4
+    const double z[5] = {1.0, za, za, 1.5, 1.5};
+    const double e[5] = {1.0, eD, eD, 1.5, 1.5};
+    std::memcpy(P.s, s, sizeof s);
+    std::memcpy(P.zeta, z, sizeof z);
+    std::memcpy(P.eta, e, sizeof e);
+    const double Tw[4] = {1.0, 0.0, 0.5, 0.5};
+    std::memcpy(P.Tw, Tw, sizeof Tw);
+    std::memcpy(P.Cw, Tw, sizeof Tw);
+    P.wall_lr = LBM_WALL_DIRICHLET;
+    P.wall_tb = LBM_WALL_ADIABATIC;
+    const char* bad = check_params(P);
+    if (bad) {
+        set_global_error("lbm_derive_params: %s (s_nu=%g zeta_a=%g eta_D=%g)", bad, s_nu, za, eD);
+        return LBM_ERR_INVALID;
+    }
+    *out = P;
+    return LBM_OK;
+}
+
+lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_ctx** out) {
+    if (!params || !out) {
+        set_global_error("lbm_create_raw: params and out must be non-NULL");
+        return LBM_ERR_INVALID;
+    }
+    *out = nullptr;
+    const char* bad = check_params(*params);
+    if (bad) {
+        set_global_error("lbm_create_raw: %s", bad);
+        return LBM_ERR_INVALID;
+    }
+    lbm_options O;
+    std::memset(&O, 0, sizeof O);
+    if (opt) O = *opt;
+    if (O.precision < LBM_F64 || O.precision > LBM_F16) {
+        set_global_error("lbm_create: unknown precision %d", O.precision);
+        return LBM_ERR_INVALID;
+    }
+    if (O.layout != LBM_AB_PULL && O.layout != LBM_AA) {
+        set_global_error("lbm_create: unknown layout %d", O.layout);
+        return LBM_ERR_INVALID;
+    }
+    if ((O.alloc == nullptr) != (O.free == nullptr)) {
+        set_global_error("lbm_create: alloc and free hooks must be given together");
+        return LBM_ERR_INVALID;
+    }
+    if (O.block_x < 0 || O.block_y < 0 || O.block_x * O.block_y > 1024 ||
+        (O.block_x && O.block_x % 32)) {
+        set_global_error("lbm_create: block_x must be a multiple of 32 and block_x*block_y <= 1024");
+        return LBM_ERR_INVALID;
+    }
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) {
+        set_global_error("lbm_create: out of host memory");
+        return LBM_ERR_NOMEM;
+    }
+    c->P = *params;
+    c->prec = O.precision;
+    c->layout = O.layout;
+    c->esz = storage_size(c->prec);
+    c->rsz = c->prec == LBM_F64 ? 8 : 4;
+    c->alloc = O.alloc;
+    c->free_fn = O.free;
+    c->alloc_user = O.alloc_user;
+    cudaGetDevice(&c->device);
+    if (O.stream) {
+        c->stream = (cudaStream_t)O.stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            lbm_status s = c->cuda_fail(e, "cudaStreamCreate");
+            delete c;
+            return s;
+        }
+        c->own_stream = true;
+    }
+    const int nx = params->nx, ny = params->ny;
+    const int per128 = (int)(128 / c->esz);
+    c->G.nx = nx;
+    c->G.ny = ny;
+    c->G.pitch = (nx + per128 - 1) / per128 * per128;
+    c->G.plane = (size_t)ny * c->G.pitch;
+    c->cd = make_coef<double>(c->P);
+    c->cf = make_coef<float>(c->P);
+    int bx = O.block_x, by = O.block_y;
+    if (bx == 0) bx = nx >= 128 ? 128 : 32;
+    if (by == 0) by = bx >= 128 ? 1 : 128 / bx;
+    c->L.bx = bx;
+    c->L.by = by;
+    c->L.stream = c->stream;
+    c->graph_chunk = O.graph_chunk == 0 ? 64 : (O.graph_chunk < 0 ? 0 : O.graph_chunk);
+    if (c->graph_chunk & 1) c->graph_chunk += 1;   // a chunk must return to the same parity
+    if (c->stream == nullptr || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread)
+        c->graph_chunk = 0;                        // the legacy stream cannot be captured
+
+    c->buf[0] = c->dalloc(c->state_bytes());
+    if (c->layout == LBM_AB_PULL) c->buf[1] = c->dalloc(c->state_bytes());
+    c->hist = c->dalloc(c->hist_bytes());
+    c->d_out = (double*)c->dalloc(64 * sizeof(double));
+    if (!c->buf[0] || (c->layout == LBM_AB_PULL && !c->buf[1]) || !c->hist || !c->d_out) {
+        lbm_status s = c->fail(LBM_ERR_NOMEM, "lbm_create: device allocation of %.3f GB failed",
+                               (2.0 * c->state_bytes() + c->hist_bytes()) / 1e9);
+        lbm_destroy(c);
+        return s;
+    }
+    // padding columns are never read, but keep them defined
+    cudaMemsetAsync(c->buf[0], 0, c->state_bytes(), c->stream);
+    if (c->buf[1]) cudaMemsetAsync(c->buf[1], 0, c->state_bytes(), c->stream);
+    cudaMemsetAsync(c->hist, 0, c->hist_bytes(), c->stream);
+
+    if ((O.T_init == nullptr) != (O.C_init == nullptr)) {
+        lbm_status s = c->fail(LBM_ERR_INVALID, "lbm_create: give both T_init and C_init");
+        lbm_destroy(c);
+        return s;
+    }
+    lbm_status s = do_init(c, O.T_init, O.C_init, O.seed, O.noise);
+    if (s == LBM_OK) {   // the caller may release T_init / C_init once create returns
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) s = c->cuda_fail(e, "lbm_create: init");
+    }
+    if (s != LBM_OK) {
+        g_last_error = c->err;
+        lbm_destroy(c);
+        return s;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(lbm_grid grid, double Ra, double Da, double eps, double Pr, double Le,
+                      double N, double J, double sigma, const lbm_options* opt, lbm_ctx** out) {
+    lbm_params P;
+    const double Ma = opt ? opt->Ma : 0.0, varpi = opt ? opt->varpi : 0.0;
+    lbm_status s = lbm_derive_params(grid, Ra, Da, eps, Pr, Le, N, J, sigma, Ma, varpi, &P);
+    if (s != LBM_OK) return s;
+    return lbm_create_raw(&P, opt, out);
+}
+
+lbm_status lbm_reset(lbm_ctx* c, const double* T_init, const double* C_init, uint64_t seed,
+                     double noise) {
+    if (!c || ((T_init == nullptr) != (C_init == nullptr))) {
+        set_global_error("lbm_reset: NULL context, or only one of T_init / C_init given");
+        return LBM_ERR_INVALID;
+    }
+    DeviceGuard dg(c->device);
+    return do_init(c, T_init, C_init, seed, noise);
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t n) {
+    if (!c || n < 0) {
+        set_global_error("lbm_step: invalid context or negative step count");
+        return LBM_ERR_INVALID;
+    }
+    DeviceGuard dg(c->device);
+    cudaError_t e = cudaSuccess;
+    // Graph replay needs the even-parity state the graph was captured from.
+    while (n > 0 && (c->t & 1) && e == cudaSuccess) {
+        e = one_step(c);
+        --n;
+    }
+    if (c->graph_chunk > 0 && n >= c->graph_chunk && e == cudaSuccess) {
+        if (!c->graph) {
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const int64_t t0 = c->t;
+                const int cur0 = c->cur;
+                cudaError_t le = cudaSuccess;
+                for (int k = 0; k < c->graph_chunk && le == cudaSuccess; ++k) le = one_step(c);
+                c->t = t0;   // capture records, it does not run
+                c->cur = cur0;
+                e = cudaStreamEndCapture(c->stream, &g);
+                if (le != cudaSuccess) e = le;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                c->graph = nullptr;
+                return c->cuda_fail(e, "lbm_step: graph capture");
+            }
+        }
+        while (n >= c->graph_chunk && e == cudaSuccess) {
+            e = cudaGraphLaunch(c->graph, c->stream);
+            c->t += c->graph_chunk;   // even chunk: buffer parity unchanged
+            n -= c->graph_chunk;
+        }
+    }
+    while (n > 0 && e == cudaSuccess) {
+        e = one_step(c);
+        --n;
+    }
+    if (e != cudaSuccess) return c->cuda_fail(e, "lbm_step");
+    return LBM_OK;
+}
+
+int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
+
+lbm_status lbm_fields(lbm_ctx* c, double* ux, double* uy, double* T, double* C, double* rho) {
+    if (!c) {
+        set_global_error("lbm_fields: NULL context");
+        return LBM_ERR_INVALID;
+    }
+    DeviceGuard dg(c->device);
+    const size_t n = c->nodes();
+    if (!c->d_fields) {
+        c->d_fields = (double*)c->dalloc(5 * n * sizeof(double));
+        if (!c->d_fields) return c->fail(LBM_ERR_NOMEM, "lbm_fields: no device memory for read-out");
+    }
+    const int mode = c->read_mode();
+    const void* b = cur_buf(c);
+    cudaError_t e = LBM_DISPATCH(c, launch_fields<double>(b, c->G, c->cd, mode, c->d_fields, c->stream),
+                                 launch_fields<float>(b, c->G, c->cf, mode, c->d_fields, c->stream),
+                                 launch_fields<__nv_bfloat16>(b, c->G, c->cf, mode, c->d_fields, c->stream),
+                                 launch_fields<__half>(b, c->G, c->cf, mode, c->d_fields, c->stream));
+    double* outs[5] = {ux, uy, T, C, rho};
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+        if (outs[k])
+            e = cudaMemcpyAsync(outs[k], c->d_fields + k * n, n * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "lbm_fields");
+    return LBM_OK;
+}
+
+lbm_status lbm_nusselt_sherwood(lbm_ctx* c, double out[4]) {
+    if (!c || !out) {
+        set_global_error("lbm_nusselt_sherwood: NULL argument");
+        return LBM_ERR_INVALID;
+    }
+    DeviceGuard dg(c->device);
+    WallSpec W;
+    W.Tw[0] = c->P.Tw[0];
+    W.Tw[1] = c->P.Tw[1];
+    W.Cw[0] = c->P.Cw[0];
+    W.Cw[1] = c->P.Cw[1];
+    W.T0 = c->P.T0;
+    W.C0 = c->P.C0;
+    W.dT = c->P.Tw[0] - c->P.Tw[1];
+    W.dC = c->P.Cw[0] - c->P.Cw[1];
+    W.L = c->P.nx;
+    const int mode = c->read_mode();
+    const void* b = cur_buf(c);
+    cudaError_t e = LBM_DISPATCH(c, launch_nush<double>(b, c->G, c->cd, mode, W, c->d_out, c->stream),
+                                 launch_nush<float>(b, c->G, c->cf, mode, W, c->d_out, c->stream),
+                                 launch_nush<__nv_bfloat16>(b, c->G, c->cf, mode, W, c->d_out, c->stream),
+                                 launch_nush<__half>(b, c->G, c->cf, mode, W, c->d_out, c->stream));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, c->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "lbm_nusselt_sherwood");
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(out[k]))
+            return c->fail(LBM_ERR_DIVERGED, "lbm_nusselt_sherwood: non-finite result at t=%lld",
+                           (long long)c->t);
+    return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_ctx* c, double* r) {
+    if (!c || !r) {
+        set_global_error("lbm_residual: NULL argument");
+        return LBM_ERR_INVALID;
+    }
+    DeviceGuard dg(c->device);
+    const size_t n = c->nodes();
+    const int nb = residual_blocks(c->G);
+    if (!c->d_snap) {
+        c->d_snap = (double*)c->dalloc(4 * n * sizeof(double));
+        c->d_partial = (double*)c->dalloc((size_t)nb * 9 * sizeof(double));
+        if (!c->d_snap || !c->d_partial) return c->fail(LBM_ERR_NOMEM, "lbm_residual: no device memory");
+    }
+    const int mode = c->read_mode();
+    const void* b = cur_buf(c);
+    double* o = c->d_out + 8;
+    cudaError_t e = LBM_DISPATCH(
+        c, launch_residual<double>(b, c->G, c->cd, mode, c->d_snap, c->d_partial, o, c->stream),
+        launch_residual<float>(b, c->G, c->cf, mode, c->d_snap, c->d_partial, o, c->stream),
+        launch_residual<__nv_bfloat16>(b, c->G, c->cf, mode, c->d_snap, c->d_partial, o, c->stream),
+        launch_residual<__half>(b, c->G, c->cf, mode, c->d_snap, c->d_partial, o, c->stream));
+    double h[9];
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, o, 9 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "lbm_residual");
+    if (h[8] != 0.0) return c->fail(LBM_ERR_DIVERGED, "lbm_residual: non-finite field at t=%lld", (long long)c->t);
+    double res = 0.0;
+    for (int q = 0; q < 4; ++q) {
+        double rq = h[4 + q] > 0 ? h[q] / h[4 + q] : (h[q] > 0 ? INFINITY : 0.0);
+        res = rq > res ? rq : res;
+    }
+    *r = c->snap_valid ? res : INFINITY;
+    c->snap_valid = true;
+    return LBM_OK;
+}
+
+// Checkpoint layout: header, then the 19 state planes, then the 4 history planes.
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t version, nx, ny, prec, layout, pitch;
+    int64_t t;
+    lbm_params P;
+};
+}  // namespace
+
+lbm_status lbm_save(lbm_ctx* c, void* buf, size_t* len) {
+    if (!c || !len) {
+        set_global_error("lbm_save: NULL argument");
+        return LBM_ERR_INVALID;
+    }
+    const size_t need = sizeof(CkptHeader) + c->state_bytes() + c->hist_bytes();
+    if (!buf) {
+        *len = need;
+        return LBM_OK;
+    }
+    if (*len < need) return c->fail(LBM_ERR_INVALID, "lbm_save: buffer of %zu bytes, need %zu", *len, need);
+    DeviceGuard dg(c->device);
+    CkptHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "LBMDDC1", 8);
+    h.version = 1;
+    h.nx = c->G.nx;
+    h.ny = c->G.ny;
+    h.prec = c->prec;
+    h.layout = c->layout;
+    h.pitch = c->G.pitch;
+    h.t = c->t;
+    h.P = c->P;
+    std::memcpy(buf, &h, sizeof h);
+    char* p = (char*)buf + sizeof h;
+    cudaError_t e = cudaMemcpyAsync(p, cur_buf(c), c->state_bytes(), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p + c->state_bytes(), c->hist, c->hist_bytes(), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "lbm_save");
+    *len = need;
+    return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_ctx* c, const void* buf, size_t len) {
+    if (!c || !buf) {
+        set_global_error("lbm_load: NULL argument");
+        return LBM_ERR_INVALID;
+    }
+    const size_t need = sizeof(CkptHeader) + c->state_bytes() + c->hist_bytes();
+    CkptHeader h;
+    if (len < sizeof h) return c->fail(LBM_ERR_INVALID, "lbm_load: truncated checkpoint");
+    std::memcpy(&h, buf, sizeof h);
+    if (std::memcmp(h.magic, "LBMDDC1", 8) != 0 || h.version != 1)
+        return c->fail(LBM_ERR_INVALID, "lbm_load: not a checkpoint of this library");
+    if (h.nx != c->G.nx || h.ny != c->G.ny || h.prec != c->prec || h.layout != c->layout ||
+        h.pitch != c->G.pitch || len < need)
+        return c->fail(LBM_ERR_INVALID, "lbm_load: checkpoint does not match this context");
+    DeviceGuard dg(c->device);
+    // the two-buffer layout keeps the state in buffer (t mod 2), which the captured graph relies on
+    const int slot = c->layout == LBM_AB_PULL ? (int)(h.t & 1) : 0;
+    const char* p = (const char*)buf + sizeof h;
+    cudaError_t e = cudaMemcpyAsync(c->buf[slot], p, c->state_bytes(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->hist, p + c->state_bytes(), c->hist_bytes(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "lbm_load");
+    c->P = h.P;
+    c->cd = make_coef<double>(c->P);
+    c->cf = make_coef<float>(c->P);
+    if (c->graph) {   // constants are baked into the captured launches
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    c->t = h.t;
+    c->cur = slot;
+    c->snap_valid = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_params(const lbm_ctx* c, lbm_params* out) {
+    if (!c || !out) {
+        set_global_error("lbm_get_params: NULL argument");
+        return LBM_ERR_INVALID;
+    }
+    *out = c->P;
+    return LBM_OK;
+}
+
+size_t lbm_device_bytes(const lbm_ctx* c) { return c ? c->bytes : 0; }
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    DeviceGuard dg(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->dfree(c->buf[0], c->state_bytes());
+    c->dfree(c->buf[1], c->state_bytes());
+    c->dfree(c->hist, c->hist_bytes());
+    c->dfree(c->d_out, 64 * sizeof(double));
+    c->dfree(c->d_fields, 5 * c->nodes() * sizeof(double));
+    c->dfree(c->d_snap, 4 * c->nodes() * sizeof(double));
+    c->dfree(c->d_partial, (size_t)residual_blocks(c->G) * 9 * sizeof(double));
+    c->dfree(c->d_stage, 2 * c->nodes() * sizeof(double));
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) {
+    if (c) return c->err.c_str();
+    return g_last_error.c_str();
+}
+
+}  // extern "C"

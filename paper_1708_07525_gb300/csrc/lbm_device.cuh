@@ -1,0 +1,218 @@
+// Device-side building blocks of the fused three-lattice step.
+//
+// Storage holds deviations from the rest equilibria (u = 0, rho = rho0,
+// T = T0, C = C0) of Eqs. 20 and 28:
+//   f'_i = f_i - w_i rho0,  g'_i = g_i - g_i^eq(T0, 0),  h'_i = h_i - h_i^eq(C0, 0).
+// Every equilibrium moment that is linear in rho, T or C (Eqs. 14, 24, 25)
+// has its rest part cancelled exactly by the shift, so the collision below
+// is the paper's collision rewritten in these variables (no approximation);
+// it keeps small numbers small, which is what FP32 / FP16 / BF16 storage needs.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// D2Q9 velocities (Eq. 8), same ordering as the paper; D2Q5 uses q = 0..4.
+//   q : 0  1  2  3  4  5  6  7  8
+//   ex: 0  1  0 -1  0  1 -1 -1  1
+//   ey: 0  0  1  0 -1  1  1 -1 -1
+__host__ __device__ constexpr int ex_of(int q) {
+    return q == 1 || q == 5 || q == 8 ? 1 : (q == 3 || q == 6 || q == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int ey_of(int q) {
+    return q == 2 || q == 5 || q == 6 ? 1 : (q == 4 || q == 7 || q == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp_of(int q) {
+    return q == 0 ? 0 : (q <= 4 ? ((q + 1) & 3) + 1 : ((q - 3) & 3) + 5);
+}
+static_assert(opp_of(1) == 3 && opp_of(3) == 1 && opp_of(2) == 4 && opp_of(4) == 2, "opp");
+static_assert(opp_of(5) == 7 && opp_of(7) == 5 && opp_of(6) == 8 && opp_of(8) == 6, "opp");
+
+// Plane index of each lattice inside the 19-plane state: f 0..8, g 9..13, h 14..18.
+constexpr int QF = 0, QG = 9, QH = 14, NQ = 19;
+
+// ---- storage conversions -------------------------------------------------------
+template <typename S> struct Store;
+template <> struct Store<double> {
+    __device__ static double ld(const double* p) { return *p; }
+    __device__ static void st(double* p, double v) { *p = v; }
+};
+template <> struct Store<float> {
+    __device__ static float ld(const float* p) { return *p; }
+    __device__ static void st(float* p, float v) { *p = v; }
+};
+template <> struct Store<__nv_bfloat16> {
+    __device__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <> struct Store<__half> {
+    __device__ static float ld(const __half* p) { return __half2float(*p); }
+    __device__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+
+// Compute type for a storage type: FP64 stays FP64, everything else is FP32.
+template <typename S> struct Real { using type = float; };
+template <> struct Real<double> { using type = double; };
+
+// ---- per-instance constants (prepared on the host, passed by value) ------------
+template <typename R>
+struct Coef {
+    R T0, C0;
+    R inv_sigma, inv_eps;      // Eq. 26
+    R eps, half_eps;           // eps of Eqs. 5, 14, 15, 19
+    R inv_eps_f;               // 1/eps for the flow equilibria (Eqs. 14, 15)
+    R gbT, gbC, Gx;            // Eq. 6 (+ optional constant Gx)
+    R l0, l0sq, l1;            // Eq. 19
+    R drag_lin, drag_quad;     // eps nu / K and eps F_eps / sqrt(K) (Eq. 5)
+    R s1, s2, s3, s4, s5, s6, s7, s8;   // Lambda (s_rho plays no role: m_0 is conserved)
+    R za1, za2, za3, za4;      // Theta (zeta_0 plays no role)
+    R ed1, ed2, ed3, ed4;      // Q
+    R c3T, c3C;                // 5 varpi - 4 sigma, 5 varpi - 4 eps (Eqs. 24, 25)
+    // Per wall side (0 left, 1 right, 2 bottom, 3 top): 2 w~ (Phi_w - Phi0) with
+    // w~ = varpi / 4, the anti-bounce-back constant in deviations.
+    R wallT[4], wallC[4];
+    int dirichlet_mask;        // bit s set: side s is Dirichlet for g and h, else adiabatic
+};
+
+template <typename R> __device__ __forceinline__ R sqrt_(R x);
+template <> __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+
+// Macroscopic quantities of one node from pre-collision deviations.
+template <typename R>
+struct Macro {
+    R rho, ux, uy, Tp, Cp, Fx, Fy;   // rho' (deviation), u, T - T0, C - C0, F
+};
+
+template <typename R>
+__device__ __forceinline__ Macro<R> macro(const Coef<R>& c, const R f[9], const R g[5],
+                                          const R h[5]) {
+    Macro<R> o;
+    R rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];  // Eq. 16
+    R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    R Tp = (((g[0] + g[1]) + (g[2] + g[3])) + g[4]) * c.inv_sigma;   // Eq. 26
+    R Cp = (((h[0] + h[1]) + (h[2] + h[3])) + h[4]) * c.inv_eps;
+    R Gy = c.gbT * Tp + c.gbC * Cp;                                  // Eq. 6
+    R vx = jx + c.half_eps * c.Gx;                                   // Eq. 19, rho0 = 1
+    R vy = jy + c.half_eps * Gy;
+    R vm = sqrt_(vx * vx + vy * vy);
+    R den = c.l0 + sqrt_(c.l0sq + c.l1 * vm);                       // Eq. 18
+    R ux = vx / den, uy = vy / den;
+    R um = sqrt_(ux * ux + uy * uy);
+    R drag = c.drag_lin + c.drag_quad * um;                          // Eq. 5
+    o.rho = rho;
+    o.ux = ux;
+    o.uy = uy;
+    o.Tp = Tp;
+    o.Cp = Cp;
+    o.Fx = c.eps * c.Gx - drag * ux;
+    o.Fy = c.eps * Gy - drag * uy;
+    return o;
+}
+
+// D2Q5 collision in moment space (Eq. 21 / 22 with Eq. 24 / 25 and the
+// moment-space source (0, X_x, X_y, 0, 0) of Eq. 27), in deviations, with the
+// inverse transform written through the orthogonality of N (N^-1 = N^T D^-1,
+// D = diag(5, 2, 2, 20, 4)).
+template <typename R>
+__device__ __forceinline__ void collide_d2q5(R d[5], R Pp, R P, R ux, R uy, R Xx, R Xy,
+                                             R r1, R r2, R r3, R r4, R c3) {
+    // Pp = Phi - Phi0, P = Phi (Phi = T or C); c3 = 5 varpi - 4 cap
+    R n0 = (((d[0] + d[1]) + (d[2] + d[3])) + d[4]);   // = cap * Pp, conserved
+    R n1 = d[1] - d[3];
+    R n2 = d[2] - d[4];
+    R n3 = ((d[1] + d[2]) + (d[3] + d[4])) - R(4) * d[0];
+    R n4 = (d[1] - d[2]) + (d[3] - d[4]);
+    n1 = n1 - r1 * (n1 - ux * P) + (R(1) - R(0.5) * r1) * Xx;
+    n2 = n2 - r2 * (n2 - uy * P) + (R(1) - R(0.5) * r2) * Xy;
+    n3 = n3 - r3 * (n3 - c3 * Pp);
+    n4 = n4 - r4 * n4;
+    R b0 = n0 * R(0.2), b1 = n1 * R(0.5), b2 = n2 * R(0.5), b3 = n3 * R(0.05), b4 = n4 * R(0.25);
+    d[0] = b0 - R(4) * b3;
+    d[1] = b0 + b1 + b3 + b4;
+    d[2] = b0 + b2 + b3 - b4;
+    d[3] = b0 - b1 + b3 + b4;
+    d[4] = b0 - b2 + b3 - b4;
+}
+
+// The full collision of one node, in place on f, g, h (deviations).
+// hist = (T u_x, T u_y, C u_x, C u_y) at the previous step; updated.
+template <typename R>
+__device__ __forceinline__ void collide(const Coef<R>& c, R f[9], R g[5], R h[5], R hist[4]) {
+    Macro<R> M = macro(c, f, g, h);
+    const R ux = M.ux, uy = M.uy, Fx = M.Fx, Fy = M.Fy, rho = M.rho;
+    const R ie = c.inv_eps_f;
+    // m = M f (Eq. 13), deviation part
+    R fa = (f[1] + f[2]) + (f[3] + f[4]);
+    R fd = (f[5] + f[6]) + (f[7] + f[8]);
+    R m1 = R(2) * fd - fa - R(4) * f[0];
+    R m2 = R(4) * f[0] - R(2) * fa + fd;
+    R m3 = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    R m4 = R(2) * (f[3] - f[1]) + (f[5] - f[6]) + (f[8] - f[7]);
+    R m5 = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    R m6 = R(2) * (f[4] - f[2]) + (f[5] + f[6]) - (f[7] + f[8]);
+    R m7 = (f[1] - f[2]) + (f[3] - f[4]);
+    R m8 = (f[5] - f[6]) + (f[7] - f[8]);
+    // m_eq (Eq. 14, alpha1 = 1, alpha2 = -3, rho0 = 1) minus its rest part, and S (Eq. 15)
+    R u2e = (ux * ux + uy * uy) * ie;
+    R uF = (ux * Fx + uy * Fy) * ie;
+    R e1 = R(-2) * rho + R(3) * u2e;
+    R e2 = rho - R(3) * u2e;
+    R e7 = (ux * ux - uy * uy) * ie;
+    R e8 = ux * uy * ie;
+    R S1 = R(6) * uF;
+    R S7 = R(2) * (ux * Fx - uy * Fy) * ie;
+    R S8 = (ux * Fy + uy * Fx) * ie;
+    // Eq. 10
+    m1 = m1 - c.s1 * (m1 - e1) + (R(1) - R(0.5) * c.s1) * S1;
+    m2 = m2 - c.s2 * (m2 - e2) - (R(1) - R(0.5) * c.s2) * S1;
+    m3 = m3 - c.s3 * (m3 - ux) + (R(1) - R(0.5) * c.s3) * Fx;
+    m4 = m4 - c.s4 * (m4 + ux) - (R(1) - R(0.5) * c.s4) * Fx;
+    m5 = m5 - c.s5 * (m5 - uy) + (R(1) - R(0.5) * c.s5) * Fy;
+    m6 = m6 - c.s6 * (m6 + uy) - (R(1) - R(0.5) * c.s6) * Fy;
+    m7 = m7 - c.s7 * (m7 - e7) + (R(1) - R(0.5) * c.s7) * S7;
+    m8 = m8 - c.s8 * (m8 - e8) + (R(1) - R(0.5) * c.s8) * S8;
+    // f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+    R a0 = rho * R(1.0 / 9.0), a1 = m1 * R(1.0 / 36.0), a2 = m2 * R(1.0 / 36.0);
+    R a3 = m3 * R(1.0 / 6.0), a4 = m4 * R(1.0 / 12.0), a5 = m5 * R(1.0 / 6.0);
+    R a6 = m6 * R(1.0 / 12.0), a7 = m7 * R(0.25), a8 = m8 * R(0.25);
+    R axis = a0 - a1 - R(2) * a2;
+    R diag = a0 + R(2) * a1 + a2;
+    R px = a3 - R(2) * a4, py = a5 - R(2) * a6;
+    R qx = a3 + a4, qy = a5 + a6;
+    f[0] = a0 - R(4) * a1 + R(4) * a2;
+    f[1] = axis + px + a7;
+    f[2] = axis + py - a7;
+    f[3] = axis - px + a7;
+    f[4] = axis - py - a7;
+    f[5] = diag + qx + qy + a8;
+    f[6] = diag - qx + qy - a8;
+    f[7] = diag - qx - qy + a8;
+    f[8] = diag + qx - qy - a8;
+    // Eq. 27 with d(Phi u)/dt = (Phi u)|t - (Phi u)|t-1 (Sec. 3.2)
+    R T = c.T0 + M.Tp, C = c.C0 + M.Cp;
+    R Tux = T * ux, Tuy = T * uy, Cux = C * ux, Cuy = C * uy;
+    R XTx = Tux - hist[0], XTy = Tuy - hist[1], XCx = Cux - hist[2], XCy = Cuy - hist[3];
+    hist[0] = Tux;
+    hist[1] = Tuy;
+    hist[2] = Cux;
+    hist[3] = Cuy;
+    collide_d2q5(g, M.Tp, T, ux, uy, XTx, XTy, c.za1, c.za2, c.za3, c.za4, c.c3T);
+    collide_d2q5(h, M.Cp, C, ux, uy, XCx, XCy, c.ed1, c.ed2, c.ed3, c.ed4, c.c3C);
+}
+
+// ---- SplitMix64 (Steele, Lea & Flood 2014): k-th output of a generator seeded with s
+__host__ __device__ inline uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ inline double uniform01(uint64_t seed, uint64_t k) {
+    return (double)(splitmix64_at(seed, k) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+}  // namespace lbm

@@ -1,0 +1,396 @@
+// Kernels of the fused three-lattice step and its read-outs.  Included by the
+// per-precision translation units, which instantiate them.
+#pragma once
+#include "lbm_device.cuh"
+#include "lbm_launch.h"
+
+namespace lbm {
+
+// Which wall a link crosses.  Sides: 0 left (x = 0), 1 right (x = nx),
+// 2 bottom (y = 0), 3 top (y = ny).
+// A population pulled along direction q from x - e_q crosses the wall behind it:
+__host__ __device__ constexpr int pull_side(int q) {
+    return q == 1 ? 0 : q == 3 ? 1 : q == 2 ? 2 : 3;
+}
+// A population pushed along direction q to x + e_q crosses the wall ahead of it:
+__host__ __device__ constexpr int push_side(int q) {
+    return q == 1 ? 1 : q == 3 ? 0 : q == 2 ? 3 : 2;
+}
+
+template <typename R>
+__device__ __forceinline__ R wall_value(const Coef<R>& c, const R* wall, int side, R reflected) {
+    // Dirichlet (anti-bounce-back, in deviations): -g*_opp + 2 w~ (Phi_w - Phi0);
+    // adiabatic (bounce-back): g*_opp.
+    return ((c.dirichlet_mask >> side) & 1) ? wall[side] - reflected : reflected;
+}
+
+// Pre-collision populations of node (i, j) at level t from a buffer of level
+// t-1 post-collision values (pull streaming, Eq. 11, with the halfway wall
+// rules).  SWAP = false: two-buffer layout, slot q of the source node.
+// SWAP = true: in-place AA layout after an even step, slot opp(q) of the source.
+template <bool SWAP, bool WITH_F, typename S, typename R>
+__device__ __forceinline__ void gather_pull(const S* __restrict__ buf, const Geom& G, int i, int j,
+                                            const Coef<R>& c, R f[9], R g[5], R h[5]) {
+    const size_t self = (size_t)j * G.pitch + i;
+    if (WITH_F) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int si = i - ex_of(q), sj = j - ey_of(q);
+            const bool in = (unsigned)si < (unsigned)G.nx && (unsigned)sj < (unsigned)G.ny;
+            const int slot_src = SWAP ? opp_of(q) : q;
+            const int slot_self = SWAP ? q : opp_of(q);
+            const S* p = in ? buf + (size_t)(QF + slot_src) * G.plane + (size_t)sj * G.pitch + si
+                            : buf + (size_t)(QF + slot_self) * G.plane + self;
+            f[q] = Store<S>::ld(p);   // no-slip halfway bounce-back when !in
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int si = i - ex_of(q), sj = j - ey_of(q);
+        const bool in = (unsigned)si < (unsigned)G.nx && (unsigned)sj < (unsigned)G.ny;
+        const int slot_src = SWAP ? opp_of(q) : q;
+        const int slot_self = SWAP ? q : opp_of(q);
+        const size_t off = in ? (size_t)sj * G.pitch + si : self;
+        const int slot = in ? slot_src : slot_self;
+        R vg = Store<S>::ld(buf + (size_t)(QG + slot) * G.plane + off);
+        R vh = Store<S>::ld(buf + (size_t)(QH + slot) * G.plane + off);
+        if (q > 0 && !in) {
+            vg = wall_value(c, c.wallT, pull_side(q), vg);
+            vh = wall_value(c, c.wallC, pull_side(q), vh);
+        }
+        g[q] = vg;
+        h[q] = vh;
+    }
+}
+
+// Natural (in-place) pre-collision populations of node (i, j).
+template <bool WITH_F, typename S, typename R>
+__device__ __forceinline__ void gather_local(const S* __restrict__ buf, const Geom& G, int i,
+                                             int j, R f[9], R g[5], R h[5]) {
+    const size_t self = (size_t)j * G.pitch + i;
+    if (WITH_F) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) f[q] = Store<S>::ld(buf + (size_t)(QF + q) * G.plane + self);
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        g[q] = Store<S>::ld(buf + (size_t)(QG + q) * G.plane + self);
+        h[q] = Store<S>::ld(buf + (size_t)(QH + q) * G.plane + self);
+    }
+}
+
+template <bool WITH_F, typename S, typename R>
+__device__ __forceinline__ void gather(int mode, const S* __restrict__ buf, const Geom& G, int i,
+                                       int j, const Coef<R>& c, R f[9], R g[5], R h[5]) {
+    if (mode == GATHER_PULL_AB)
+        gather_pull<false, WITH_F>(buf, G, i, j, c, f, g, h);
+    else if (mode == GATHER_PULL_AA)
+        gather_pull<true, WITH_F>(buf, G, i, j, c, f, g, h);
+    else
+        gather_local<WITH_F>(buf, G, i, j, f, g, h);
+}
+
+template <typename R>
+__device__ __forceinline__ void load_hist(const R* __restrict__ hist, const Geom& G, size_t self,
+                                          R hv[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) hv[k] = hist[(size_t)k * G.plane + self];
+}
+template <typename R>
+__device__ __forceinline__ void store_hist(R* __restrict__ hist, const Geom& G, size_t self,
+                                           const R hv[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) hist[(size_t)k * G.plane + self] = hv[k];
+}
+
+// ---- the fused step, two-buffer pull layout ---------------------------------------
+template <typename S>
+__global__ void __launch_bounds__(256)
+step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
+               typename Real<S>::type* __restrict__ hist, Geom G,
+               Coef<typename Real<S>::type> c) {
+    using R = typename Real<S>::type;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    R f[9], g[5], h[5], hv[4];
+    const size_t self = (size_t)j * G.pitch + i;
+    gather_pull<false, true>(src, G, i, j, c, f, g, h);
+    load_hist(hist, G, self, hv);
+    collide(c, f, g, h, hv);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Store<S>::st(dst + (size_t)(QF + q) * G.plane + self, f[q]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        Store<S>::st(dst + (size_t)(QG + q) * G.plane + self, g[q]);
+        Store<S>::st(dst + (size_t)(QH + q) * G.plane + self, h[q]);
+    }
+    store_hist(hist, G, self, hv);
+}
+
+// ---- the fused step, in-place AA layout -------------------------------------------
+// Even step (level t even): natural pre-collision values at x -> collide ->
+// post-collision value of direction q stored in slot opp(q) of x.
+// Odd step: pull from the swapped slots of the neighbours (with wall rules),
+// collide, push post-collision value of direction q into slot q of x + e_q
+// (or, where that link crosses a wall, the reflected value into slot opp(q)
+// of x).  Each thread reads and writes the same set of locations, so the
+// update is race-free in place.
+template <typename S, bool ODD>
+__global__ void __launch_bounds__(256)
+step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
+               Coef<typename Real<S>::type> c) {
+    using R = typename Real<S>::type;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    R f[9], g[5], h[5], hv[4];
+    const size_t self = (size_t)j * G.pitch + i;
+    if (ODD)
+        gather_pull<true, true>(buf, G, i, j, c, f, g, h);
+    else
+        gather_local<true>(buf, G, i, j, f, g, h);
+    load_hist(hist, G, self, hv);
+    collide(c, f, g, h, hv);
+    if (!ODD) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            Store<S>::st(buf + (size_t)(QF + opp_of(q)) * G.plane + self, f[q]);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            Store<S>::st(buf + (size_t)(QG + opp_of(q)) * G.plane + self, g[q]);
+            Store<S>::st(buf + (size_t)(QH + opp_of(q)) * G.plane + self, h[q]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int ti = i + ex_of(q), tj = j + ey_of(q);
+            const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
+            S* p = in ? buf + (size_t)(QF + q) * G.plane + (size_t)tj * G.pitch + ti
+                      : buf + (size_t)(QF + opp_of(q)) * G.plane + self;
+            Store<S>::st(p, f[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int ti = i + ex_of(q), tj = j + ey_of(q);
+            const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
+            R vg = g[q], vh = h[q];
+            size_t off = self;
+            int slot = opp_of(q);
+            if (in) {
+                off = (size_t)tj * G.pitch + ti;
+                slot = q;
+            } else if (q > 0) {
+                vg = wall_value(c, c.wallT, push_side(q), vg);
+                vh = wall_value(c, c.wallC, push_side(q), vh);
+            }
+            Store<S>::st(buf + (size_t)(QG + slot) * G.plane + off, vg);
+            Store<S>::st(buf + (size_t)(QH + slot) * G.plane + off, vh);
+        }
+    }
+    store_hist(hist, G, self, hv);
+}
+
+// ---- initial state ---------------------------------------------------------------
+// T - T0 and C - C0 at t = 0: from caller arrays (FP64 [ny][nx]) or from the
+// SplitMix64 noise with key (field * ny + j) * nx + i.
+__device__ __forceinline__ void initial_TC(const InitSpec& I, const Geom& G, int i, int j,
+                                           double& Tp, double& Cp) {
+    const size_t k = (size_t)j * G.nx + i;
+    if (I.T_init) {
+        Tp = I.T_init[k] - I.T0;
+        Cp = I.C_init[k] - I.C0;
+    } else {
+        const size_t n = (size_t)G.nx * G.ny;
+        Tp = I.noise * (2.0 * uniform01(I.seed, k) - 1.0);
+        Cp = I.noise * (2.0 * uniform01(I.seed, n + k) - 1.0);
+    }
+}
+
+// Deviation of the D2Q5 rest equilibrium of Eq. 28 at u = 0 for Phi' = Phi - Phi0.
+__device__ __forceinline__ double eq5_dev(int q, double cap, double varpi, double Pp) {
+    return q == 0 ? (cap - varpi) * Pp : 0.25 * varpi * Pp;
+}
+
+// Writes the state at t = 0.  AB (PULL = true): the buffer must give the t = 0
+// populations when pulled, so slot q of node y holds the t = 0 population of
+// y + e_q (or, for a link that leaves the cavity, the value whose wall rule
+// gives the t = 0 population of y).  AA (PULL = false): natural slots.
+// The flow populations are at rest (f' = 0).  History = (T u, C u) of t = 0.
+template <typename S, bool PULL>
+__global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
+                            Coef<typename Real<S>::type> c, InitSpec I) {
+    using R = typename Real<S>::type;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    const size_t self = (size_t)j * G.pitch + i;
+    double Tp, Cp;
+    initial_TC(I, G, i, j, Tp, Cp);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Store<S>::st(buf + (size_t)(QF + q) * G.plane + self, R(0));
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        double vg, vh;
+        if (!PULL) {
+            vg = eq5_dev(q, I.sigma, I.varpi, Tp);
+            vh = eq5_dev(q, I.eps, I.varpi, Cp);
+        } else {
+            const int ti = i + ex_of(q), tj = j + ey_of(q);
+            if ((unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny) {
+                double Tn, Cn;
+                initial_TC(I, G, ti, tj, Tn, Cn);
+                vg = eq5_dev(q, I.sigma, I.varpi, Tn);
+                vh = eq5_dev(q, I.eps, I.varpi, Cn);
+            } else {
+                // pulled back at y along opp(q) through the wall ahead of q
+                const int o = opp_of(q), side = pull_side(o);
+                const double wg = eq5_dev(o, I.sigma, I.varpi, Tp);
+                const double wh = eq5_dev(o, I.eps, I.varpi, Cp);
+                const bool dir = (c.dirichlet_mask >> side) & 1;
+                vg = dir ? (double)c.wallT[side] - wg : wg;
+                vh = dir ? (double)c.wallC[side] - wh : wh;
+            }
+        }
+        Store<S>::st(buf + (size_t)(QG + q) * G.plane + self, (R)vg);
+        Store<S>::st(buf + (size_t)(QH + q) * G.plane + self, (R)vh);
+    }
+    // history from the t = 0 macroscopic state (Eqs. 16-19, 26)
+    R f[9], g[5], h[5];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q] = R(0);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        g[q] = (R)eq5_dev(q, I.sigma, I.varpi, Tp);
+        h[q] = (R)eq5_dev(q, I.eps, I.varpi, Cp);
+    }
+    Macro<R> M = macro(c, f, g, h);
+    R hv[4];
+    const R T = c.T0 + M.Tp, C = c.C0 + M.Cp;
+    hv[0] = T * M.ux;
+    hv[1] = T * M.uy;
+    hv[2] = C * M.ux;
+    hv[3] = C * M.uy;
+    store_hist(hist, G, self, hv);
+}
+
+// ---- read-outs -----------------------------------------------------------------------
+// Fields at the current level: out planes [5][ny][nx] = ux, uy, T, C, rho (FP64).
+template <typename S>
+__global__ void fields_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c,
+                              int mode, double* __restrict__ out) {
+    using R = typename Real<S>::type;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    R f[9], g[5], h[5];
+    gather<true>(mode, buf, G, i, j, c, f, g, h);
+    Macro<R> M = macro(c, f, g, h);
+    const size_t n = (size_t)G.nx * G.ny, k = (size_t)j * G.nx + i;
+    out[k] = (double)M.ux;
+    out[n + k] = (double)M.uy;
+    out[2 * n + k] = (double)c.T0 + (double)M.Tp;
+    out[3 * n + k] = (double)c.C0 + (double)M.Cp;
+    out[4 * n + k] = 1.0 + (double)M.rho;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Mean Nu / Sh on the left and right walls (Eq. 38), one block, FP64 sums with a
+// fixed reduction order (deterministic).  out = {Nu_L, Sh_L, Nu_R, Sh_R}.
+template <typename S>
+__global__ void __launch_bounds__(NUSH_THREADS)
+nush_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c, int mode,
+            WallSpec W, double* __restrict__ out) {
+    using R = typename Real<S>::type;
+    double acc[4] = {0, 0, 0, 0};
+    for (int j = threadIdx.x; j < G.ny; j += blockDim.x) {
+        R f[9], g[5], h[5];
+        double T[4], C[4];
+        const int cols[4] = {0, 1, G.nx - 2, G.nx - 1};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            gather<false>(mode, buf, G, cols[k], j, c, f, g, h);
+            const R sg = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+            const R sh = ((h[0] + h[1]) + (h[2] + h[3])) + h[4];
+            T[k] = W.T0 + (double)(sg * c.inv_sigma);
+            C[k] = W.C0 + (double)(sh * c.inv_eps);
+        }
+        // dPhi/dx at the wall: (-8 Phi_w + 9 Phi_0 - Phi_1) / 3, mirrored on the right
+        acc[0] += -W.L * (-8.0 * W.Tw[0] + 9.0 * T[0] - T[1]) / 3.0 / W.dT;
+        acc[1] += -W.L * (-8.0 * W.Cw[0] + 9.0 * C[0] - C[1]) / 3.0 / W.dC;
+        acc[2] += -W.L * (8.0 * W.Tw[1] - 9.0 * T[3] + T[2]) / 3.0 / W.dT;
+        acc[3] += -W.L * (8.0 * W.Cw[1] - 9.0 * C[3] + C[2]) / 3.0 / W.dC;
+    }
+    __shared__ double red[NUSH_THREADS / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s / G.ny;
+    }
+}
+
+// Residual pass 1: per node phi = (ux, uy, T, C) at the current level; per block
+// the maxima of |phi - snap| and |phi| and a non-finite flag go to
+// partial[block][9]; snap is replaced by phi.  Grid-stride over nodes.
+template <typename S>
+__global__ void __launch_bounds__(RES_THREADS)
+residual_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c, int mode,
+                double* __restrict__ snap, double* __restrict__ partial) {
+    using R = typename Real<S>::type;
+    double dmax[4] = {0, 0, 0, 0}, amax[4] = {0, 0, 0, 0}, bad = 0;
+    const size_t n = (size_t)G.nx * G.ny;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(k / G.nx), i = (int)(k - (size_t)j * G.nx);
+        R f[9], g[5], h[5];
+        gather<true>(mode, buf, G, i, j, c, f, g, h);
+        Macro<R> M = macro(c, f, g, h);
+        const double phi[4] = {(double)M.ux, (double)M.uy, (double)c.T0 + (double)M.Tp,
+                               (double)c.C0 + (double)M.Cp};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double old = snap[q * n + k];
+            if (!isfinite(phi[q])) bad = 1;
+            dmax[q] = fmax(dmax[q], fabs(phi[q] - old));
+            amax[q] = fmax(amax[q], fabs(phi[q]));
+            snap[q * n + k] = phi[q];
+        }
+    }
+    __shared__ double red[RES_THREADS / 32][9];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double v[9] = {dmax[0], dmax[1], dmax[2], dmax[3], amax[0], amax[1], amax[2], amax[3], bad};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const double r = warp_max(v[q]);
+        if (lane == 0) red[warp][q] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w][threadIdx.x]);
+        partial[(size_t)blockIdx.x * 9 + threadIdx.x] = s;
+    }
+}
+
+// Residual pass 2: one block folds partial[nblocks][9] into out[9].
+__global__ void __launch_bounds__(RES_THREADS)
+residual_final_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ out);
+
+}  // namespace lbm

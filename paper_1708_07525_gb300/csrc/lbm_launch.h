@@ -1,0 +1,66 @@
+// Host-side launch interface between the C ABI (lbm_api.cu) and the
+// per-precision kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Geometry of one state: planes of ny rows of `pitch` elements (x fastest).
+struct Geom {
+    int nx, ny;
+    int pitch;       // elements per row, rows start 128-byte aligned
+    size_t plane;    // elements per plane = ny * pitch
+};
+
+// How the pre-collision populations of the current level are read.
+enum { GATHER_LOCAL = 0, GATHER_PULL_AB = 1, GATHER_PULL_AA = 2 };
+
+struct InitSpec {
+    const double* T_init;   // device [ny][nx] or NULL (noise)
+    const double* C_init;
+    uint64_t seed;
+    double noise;
+    double T0, C0, sigma, eps, varpi;
+};
+
+struct WallSpec {
+    double Tw[2], Cw[2];    // absolute wall values, left / right
+    double T0, C0, dT, dC, L;
+};
+
+constexpr int NUSH_THREADS = 512;
+constexpr int RES_THREADS = 256;
+
+struct LaunchCfg {
+    int bx, by;
+    cudaStream_t stream;
+};
+
+// Launchers, explicitly instantiated for S = double, float, __nv_bfloat16, __half.
+template <typename S>
+cudaError_t launch_init(void* buf, void* hist, const Geom& G, const Coef<typename Real<S>::type>& c,
+                        const InitSpec& I, bool pull, cudaStream_t st);
+template <typename S>
+cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G,
+                           const Coef<typename Real<S>::type>& c, const LaunchCfg& L);
+template <typename S>
+cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
+                           const Coef<typename Real<S>::type>& c, bool odd, const LaunchCfg& L);
+template <typename S>
+cudaError_t launch_fields(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
+                          int mode, double* out, cudaStream_t st);
+template <typename S>
+cudaError_t launch_nush(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
+                        int mode, const WallSpec& W, double* out, cudaStream_t st);
+// partial must hold residual_blocks(G) * 9 doubles; out 9 doubles.
+template <typename S>
+cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
+                            int mode, double* snap, double* partial, double* out,
+                            cudaStream_t st);
+int residual_blocks(const Geom& G);
+
+}  // namespace lbm

@@ -1,0 +1,90 @@
+// Definitions of the launchers declared in lbm_launch.h (included by the
+// per-precision translation units, which instantiate them).
+#pragma once
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+inline dim3 grid_for(const Geom& G, int bx, int by) {
+    return dim3((unsigned)((G.nx + bx - 1) / bx), (unsigned)((G.ny + by - 1) / by), 1);
+}
+
+template <typename S>
+cudaError_t launch_init(void* buf, void* hist, const Geom& G, const Coef<typename Real<S>::type>& c,
+                        const InitSpec& I, bool pull, cudaStream_t st) {
+    using R = typename Real<S>::type;
+    dim3 b(128, 1), gr = grid_for(G, 128, 1);
+    if (pull)
+        init_kernel<S, true><<<gr, b, 0, st>>>((S*)buf, (R*)hist, G, c, I);
+    else
+        init_kernel<S, false><<<gr, b, 0, st>>>((S*)buf, (R*)hist, G, c, I);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G,
+                           const Coef<typename Real<S>::type>& c, const LaunchCfg& L) {
+    using R = typename Real<S>::type;
+    dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
+    step_ab_kernel<S><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
+                           const Coef<typename Real<S>::type>& c, bool odd, const LaunchCfg& L) {
+    using R = typename Real<S>::type;
+    dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
+    if (odd)
+        step_aa_kernel<S, true><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+    else
+        step_aa_kernel<S, false><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_fields(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
+                          int mode, double* out, cudaStream_t st) {
+    dim3 b(128, 1), gr = grid_for(G, 128, 1);
+    fields_kernel<S><<<gr, b, 0, st>>>((const S*)buf, G, c, mode, out);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_nush(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
+                        int mode, const WallSpec& W, double* out, cudaStream_t st) {
+    nush_kernel<S><<<1, NUSH_THREADS, 0, st>>>((const S*)buf, G, c, mode, W, out);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
+                            int mode, double* snap, double* partial, double* out,
+                            cudaStream_t st) {
+    const int nb = residual_blocks(G);
+    residual_kernel<S><<<nb, RES_THREADS, 0, st>>>((const S*)buf, G, c, mode, snap, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    residual_final_kernel<<<1, RES_THREADS, 0, st>>>(partial, nb, out);
+    return cudaGetLastError();
+}
+
+#define LBM_INSTANTIATE(S)                                                                      \
+    template cudaError_t launch_init<S>(void*, void*, const Geom&,                             \
+                                        const Coef<Real<S>::type>&, const InitSpec&, bool,     \
+                                        cudaStream_t);                                         \
+    template cudaError_t launch_step_ab<S>(const void*, void*, void*, const Geom&,             \
+                                           const Coef<Real<S>::type>&, const LaunchCfg&);      \
+    template cudaError_t launch_step_aa<S>(void*, void*, const Geom&,                          \
+                                           const Coef<Real<S>::type>&, bool,                   \
+                                           const LaunchCfg&);                                  \
+    template cudaError_t launch_fields<S>(const void*, const Geom&,                            \
+                                          const Coef<Real<S>::type>&, int, double*,            \
+                                          cudaStream_t);                                       \
+    template cudaError_t launch_nush<S>(const void*, const Geom&, const Coef<Real<S>::type>&,  \
+                                        int, const WallSpec&, double*, cudaStream_t);          \
+    template cudaError_t launch_residual<S>(const void*, const Geom&,                          \
+                                            const Coef<Real<S>::type>&, int, double*, double*, \
+                                            double*, cudaStream_t);
+
+}  // namespace lbm

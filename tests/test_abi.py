@@ -1,0 +1,73 @@
+"""CPU-side checks of the C ABI: liblbm.so builds for sm_103a, loads, exports
+every entry point include/*.h declares, and rejects invalid input before any
+device work (no GPU needed for these)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1708_07525_gb300 import build, lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(lbm\w*)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+def test_library_builds_and_exports_all_declared_symbols():
+    path = build.build()
+    L = C.CDLL(path)
+    syms = declared_symbols()
+    assert "lbm_step" in syms and "lbm_create" in syms and "lbm_nusselt_sherwood" in syms
+    missing = [s for s in syms if not hasattr(L, s)]
+    assert not missing, missing
+
+
+def test_derive_params_matches_paper_mapping():
+    """Sec. 4.1: 1/s_nu = 1/2 + Ma J L sqrt(Pr) / (c_s sqrt(Ra)), L = nx; Eq. 29; Eq. 7."""
+    p = lbm.lbm_derive_params(64, 64, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
+    cs = 1 / np.sqrt(3)
+    inv_snu = 0.5 + 0.1 * 1 * 64 * 1 / (cs * 100)
+    assert abs(p.s[7] - 1 / inv_snu) < 1e-15
+    nu = 0.1 * cs * 64 * np.sqrt(1 / 1e4)
+    assert abs(p.nu - nu) < 1e-16
+    assert abs(p.zeta[1] - 1 / (0.5 + nu / 0.2)) < 1e-14
+    assert abs(p.eta[1] - 1 / (0.5 + nu / 2 / 0.2)) < 1e-14
+    assert abs(p.Feps - 1.75 / np.sqrt(150 * 0.6 ** 3)) < 1e-15
+    assert abs(p.K - 0.01 * 64 * 64) < 1e-12
+    assert list(p.s)[:7] == [1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2]
+    assert list(p.zeta)[3:] == [1.5, 1.5] and list(p.eta)[3:] == [1.5, 1.5]
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=2), dict(eps=0.0), dict(eps=1.5), dict(Da=0.0), dict(Ra=-1.0), dict(Le=0.0),
+])
+def test_invalid_parameters_rejected(bad):
+    kw = dict(nx=16, ny=16, Ra=1e4, Da=1e-2, eps=0.6, Pr=1.0, Le=2.0, N=1.0)
+    kw.update(bad)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_derive_params(**kw)
+    assert ei.value.status == lbm.ERR_INVALID
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Cavity(**kw, allocator=None)
+    assert ei.value.status == lbm.ERR_INVALID
+
+
+def test_rate_outside_stable_range_rejected():
+    # Ra tiny at a large grid -> nu_e huge -> s_nu tiny but valid; Le huge -> eta_D near 2
+    p = lbm.lbm_derive_params(16, 16, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
+    p.s[7] = 2.0
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Cavity(params=p, allocator=None)
+    assert ei.value.status == lbm.ERR_INVALID
+    assert "relaxation rate" in str(ei.value)

@@ -1,0 +1,171 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 storage and arithmetic 1e-12 relative L2 on u, T, C; FP32
+1e-5 relative L2 after 1000 steps.  Both sides draw the initial noise from
+their own SplitMix64 implementation with the same seed and key.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1708_07525_gb300 import lbm
+from paper_1708_07525_gb300.workloads import SMALL_AIDING, CavitySpec, throughput_cavity
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("ux", "uy", "T", "C")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads(oracle_mod):
+    oracle_mod.set_threads(os.cpu_count() or 1)
+
+
+def make_pair(O, spec: CavitySpec, precision="f64", layout="ab", **kw):
+    gpu = lbm.Cavity(*spec.args(), precision=precision, layout=layout, seed=spec.seed,
+                     noise=spec.noise, **kw)
+    p = O.derive(*spec.args())
+    ora = O.Oracle(p, seed=spec.seed, noise=spec.noise)
+    return gpu, ora
+
+
+def compare(gpu, ora, tol, nush_tol=None):
+    fg = gpu.fields()
+    fo = ora.fields()
+    errs = {k: rel_l2(fg[k], fo[k]) for k in KEYS}
+    for k in KEYS:
+        assert errs[k] <= tol, (k, errs)
+    assert np.abs(fg["rho"] - fo["rho"]).max() <= 1e3 * tol
+    if nush_tol is not None:
+        ng, no = gpu.nusselt_sherwood(), ora.nusselt_sherwood()
+        np.testing.assert_allclose(ng, no, rtol=nush_tol, atol=0)
+    return errs
+
+
+SMALL = [
+    CavitySpec(3, 3, Ra=1e4, Da=1e-2, eps=0.6, Le=2.0, N=1.0, seed=11, noise=0.05),
+    CavitySpec(5, 7, Ra=1e5, Da=1e-3, eps=0.4, Le=5.0, N=-1.0, seed=12, noise=0.05),
+    CavitySpec(33, 17, Ra=1e5, Da=1e-1, eps=0.8, Le=3.0, N=2.0, sigma=1.7, seed=13, noise=0.02),
+    CavitySpec(130, 67, Ra=3e4, Da=1e-2, eps=0.5, Le=0.7, N=-2.0, sigma=0.6, seed=14, noise=0.01),
+]
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("nsteps", [0, 1, 2, 3])
+def test_first_steps_f64(oracle_mod, layout, nsteps):
+    """Initial state and the first steps (pull initialisation, AA parity)."""
+    spec = SMALL[2]
+    gpu, ora = make_pair(oracle_mod, spec, "f64", layout)
+    gpu.step(nsteps)
+    ora.step(nsteps)
+    assert gpu.t == nsteps
+    compare(gpu, ora, 1e-13, nush_tol=1e-13)
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("spec", SMALL, ids=lambda s: f"{s.nx}x{s.ny}")
+def test_f64_1000_steps(oracle_mod, spec, layout):
+    gpu, ora = make_pair(oracle_mod, spec, "f64", layout)
+    gpu.step(1000)
+    ora.step(1000)
+    compare(gpu, ora, 1e-12, nush_tol=1e-11)
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+@pytest.mark.parametrize("spec", SMALL[1:], ids=lambda s: f"{s.nx}x{s.ny}")
+def test_f32_1000_steps(oracle_mod, spec, layout):
+    gpu, ora = make_pair(oracle_mod, spec, "f32", layout)
+    gpu.step(1000)
+    ora.step(1000)
+    compare(gpu, ora, 1e-5)
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_small_aiding_cavity_10000_steps_f64(oracle_mod, layout):
+    """64 x 64 porous cavity, Ra = 1e4, Da = 1e-2, eps = 0.6, Le = 2, N = 1, FP64."""
+    gpu, ora = make_pair(oracle_mod, SMALL_AIDING, "f64", layout)
+    gpu.step(10000)
+    ora.step(10000)
+    compare(gpu, ora, 1e-12, nush_tol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["f32"])
+def test_small_aiding_cavity_1000_steps_f32(oracle_mod, precision):
+    gpu, ora = make_pair(oracle_mod, SMALL_AIDING, precision, "ab")
+    gpu.step(1000)
+    ora.step(1000)
+    compare(gpu, ora, 1e-5)
+
+
+def test_throughput_cavity_full_size_f32(oracle_mod):
+    """4096^2 opposing-buoyancy cavity in FP32, the benchmark's launch
+    configuration (two-buffer pull, default tile, graph replay), against the
+    oracle over a short run on the whole grid."""
+    spec = throughput_cavity(4096)
+    gpu, ora = make_pair(oracle_mod, spec, "f32", "ab")
+    n = 4
+    gpu.step(n)
+    ora.step(n)
+    compare(gpu, ora, 1e-5)
+
+
+def test_graph_and_tile_invariance_bitwise(oracle_mod):
+    spec = SMALL[3]
+    a = lbm.Cavity(*spec.args(), precision="f32", seed=spec.seed, noise=spec.noise, graph_chunk=-1)
+    b = lbm.Cavity(*spec.args(), precision="f32", seed=spec.seed, noise=spec.noise, graph_chunk=16,
+                   block=(32, 4))
+    a.step(101)
+    b.step(101)
+    fa, fb = a.fields(), b.fields()
+    for k in KEYS:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_checkpoint_resume_bitwise(layout):
+    spec = SMALL[2]
+    a = lbm.Cavity(*spec.args(), precision="f32", layout=layout, seed=spec.seed, noise=spec.noise)
+    a.step(333)
+    blob = a.save()
+    a.step(400)
+    b = lbm.Cavity(*spec.args(), precision="f32", layout=layout, seed=99, noise=spec.noise)
+    b.load(blob)
+    assert b.t == 333
+    b.step(400)
+    fa, fb = a.fields(), b.fields()
+    for k in KEYS:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_user_initial_fields_match_oracle(oracle_mod):
+    from paper_1708_07525_gb300.workloads import random_fields
+    spec = SMALL[2]
+    T, Cc = random_fields(spec.nx, spec.ny, seed=5, amp=0.05)
+    gpu = lbm.Cavity(*spec.args(), precision="f64", T_init=T, C_init=Cc)
+    ora = oracle_mod.Oracle(oracle_mod.derive(*spec.args()), T_init=T, C_init=Cc)
+    fg = gpu.fields()
+    assert np.abs(fg["T"] - T).max() < 1e-15 and np.abs(fg["C"] - Cc).max() < 1e-15
+    gpu.step(200)
+    ora.step(200)
+    compare(gpu, ora, 1e-12)
+
+
+def test_residual_and_divergence_flag():
+    spec = SMALL_AIDING
+    g = lbm.Cavity(*spec.args(), precision="f32", seed=1)
+    assert g.residual() == float("inf")
+    g.step(100)
+    r1 = g.residual()
+    assert 0 < r1 < 1
+    p = lbm.lbm_derive_params(16, 16, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
+    p.gbT = 50.0   # absurd buoyancy: the state blows up to non-finite values
+    bad = lbm.Cavity(params=p, precision="f32", noise=0.1)
+    bad.step(2000)
+    with pytest.raises(lbm.LbmError) as ei:
+        bad.residual()
+    assert ei.value.status == lbm.ERR_DIVERGED
