@@ -113,89 +113,92 @@ __device__ __forceinline__ Macro<R> macro(const Coef<R>& c, const R f[9], const 
     return o;
 }
 
-// D2Q5 collision in moment space (Eq. 21 / 22 with Eq. 24 / 25 and the
-// moment-space source (0, X_x, X_y, 0, 0) of Eq. 27), in deviations, with the
-// inverse transform written through the orthogonality of N (N^-1 = N^T D^-1,
-// D = diag(5, 2, 2, 20, 4)).
+// D2Q5 collision (Eq. 21 / 22 with Eq. 24 / 25 and the moment-space source
+// (0, X_x, X_y, 0, 0) of Eq. 27), written as d* = d - N^-1 [Theta (n - n_eq)
+// - (I - Theta/2) S] so that only the change is rounded; the zeroth moment
+// (cap * Phi) is conserved exactly, its change is set to zero.  N^-1 uses the
+// orthogonality of N: N^-1 = N^T D^-1, D = diag(5, 2, 2, 20, 4).
+// Pp = Phi - Phi0, P = Phi (Phi = T or C), c3 = 5 varpi - 4 cap.
 template <typename R>
 __device__ __forceinline__ void collide_d2q5(R d[5], R Pp, R P, R ux, R uy, R Xx, R Xy,
                                              R r1, R r2, R r3, R r4, R c3) {
-    // Pp = Phi - Phi0, P = Phi (Phi = T or C); c3 = 5 varpi - 4 cap
-    R n0 = (((d[0] + d[1]) + (d[2] + d[3])) + d[4]);   // = cap * Pp, conserved
-    R n1 = d[1] - d[3];
-    R n2 = d[2] - d[4];
-    R n3 = ((d[1] + d[2]) + (d[3] + d[4])) - R(4) * d[0];
-    R n4 = (d[1] - d[2]) + (d[3] - d[4]);
-    n1 = n1 - r1 * (n1 - ux * P) + (R(1) - R(0.5) * r1) * Xx;
-    n2 = n2 - r2 * (n2 - uy * P) + (R(1) - R(0.5) * r2) * Xy;
-    n3 = n3 - r3 * (n3 - c3 * Pp);
-    n4 = n4 - r4 * n4;
-    R b0 = n0 * R(0.2), b1 = n1 * R(0.5), b2 = n2 * R(0.5), b3 = n3 * R(0.05), b4 = n4 * R(0.25);
-    d[0] = b0 - R(4) * b3;
-    d[1] = b0 + b1 + b3 + b4;
-    d[2] = b0 + b2 + b3 - b4;
-    d[3] = b0 - b1 + b3 + b4;
-    d[4] = b0 - b2 + b3 - b4;
+    const R n1 = d[1] - d[3];
+    const R n2 = d[2] - d[4];
+    const R n3 = ((d[1] + d[2]) + (d[3] + d[4])) - R(4) * d[0];
+    const R n4 = (d[1] - d[2]) + (d[3] - d[4]);
+    const R k1 = r1 * (n1 - ux * P) - (R(1) - R(0.5) * r1) * Xx;
+    const R k2 = r2 * (n2 - uy * P) - (R(1) - R(0.5) * r2) * Xy;
+    const R k3 = r3 * (n3 - c3 * Pp);
+    const R k4 = r4 * n4;
+    const R b1 = k1 * R(0.5), b2 = k2 * R(0.5), b3 = k3 * R(0.05), b4 = k4 * R(0.25);
+    d[0] += R(4) * b3;
+    d[1] -= b1 + b3 + b4;
+    d[2] -= b2 + b3 - b4;
+    d[3] -= -b1 + b3 + b4;
+    d[4] -= -b2 + b3 - b4;
 }
 
 // The full collision of one node, in place on f, g, h (deviations).
 // hist = (T u_x, T u_y, C u_x, C u_y) at the previous step; updated.
+// The D2Q9 part is Eq. 10 written as f* = f - M^-1 [Lambda (m - m_eq) - (I - Lambda/2) S]
+// (only the change is rounded; the density moment is conserved exactly).
 template <typename R>
 __device__ __forceinline__ void collide(const Coef<R>& c, R f[9], R g[5], R h[5], R hist[4]) {
     Macro<R> M = macro(c, f, g, h);
     const R ux = M.ux, uy = M.uy, Fx = M.Fx, Fy = M.Fy, rho = M.rho;
     const R ie = c.inv_eps_f;
-    // m = M f (Eq. 13), deviation part
-    R fa = (f[1] + f[2]) + (f[3] + f[4]);
-    R fd = (f[5] + f[6]) + (f[7] + f[8]);
-    R m1 = R(2) * fd - fa - R(4) * f[0];
-    R m2 = R(4) * f[0] - R(2) * fa + fd;
-    R m3 = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    R m4 = R(2) * (f[3] - f[1]) + (f[5] - f[6]) + (f[8] - f[7]);
-    R m5 = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    R m6 = R(2) * (f[4] - f[2]) + (f[5] + f[6]) - (f[7] + f[8]);
-    R m7 = (f[1] - f[2]) + (f[3] - f[4]);
-    R m8 = (f[5] - f[6]) + (f[7] - f[8]);
+    // m = M f (Eq. 13), deviation part; m_0 = rho' is not needed
+    const R fa = (f[1] + f[2]) + (f[3] + f[4]);
+    const R fd = (f[5] + f[6]) + (f[7] + f[8]);
+    const R m1 = R(2) * fd - fa - R(4) * f[0];
+    const R m2 = R(4) * f[0] - R(2) * fa + fd;
+    const R m3 = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const R m4 = R(2) * (f[3] - f[1]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const R m5 = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const R m6 = R(2) * (f[4] - f[2]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const R m7 = (f[1] - f[2]) + (f[3] - f[4]);
+    const R m8 = (f[5] - f[6]) + (f[7] - f[8]);
     // m_eq (Eq. 14, alpha1 = 1, alpha2 = -3, rho0 = 1) minus its rest part, and S (Eq. 15)
-    R u2e = (ux * ux + uy * uy) * ie;
-    R uF = (ux * Fx + uy * Fy) * ie;
-    R e1 = R(-2) * rho + R(3) * u2e;
-    R e2 = rho - R(3) * u2e;
-    R e7 = (ux * ux - uy * uy) * ie;
-    R e8 = ux * uy * ie;
-    R S1 = R(6) * uF;
-    R S7 = R(2) * (ux * Fx - uy * Fy) * ie;
-    R S8 = (ux * Fy + uy * Fx) * ie;
-    // Eq. 10
-    m1 = m1 - c.s1 * (m1 - e1) + (R(1) - R(0.5) * c.s1) * S1;
-    m2 = m2 - c.s2 * (m2 - e2) - (R(1) - R(0.5) * c.s2) * S1;
-    m3 = m3 - c.s3 * (m3 - ux) + (R(1) - R(0.5) * c.s3) * Fx;
-    m4 = m4 - c.s4 * (m4 + ux) - (R(1) - R(0.5) * c.s4) * Fx;
-    m5 = m5 - c.s5 * (m5 - uy) + (R(1) - R(0.5) * c.s5) * Fy;
-    m6 = m6 - c.s6 * (m6 + uy) - (R(1) - R(0.5) * c.s6) * Fy;
-    m7 = m7 - c.s7 * (m7 - e7) + (R(1) - R(0.5) * c.s7) * S7;
-    m8 = m8 - c.s8 * (m8 - e8) + (R(1) - R(0.5) * c.s8) * S8;
-    // f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-    R a0 = rho * R(1.0 / 9.0), a1 = m1 * R(1.0 / 36.0), a2 = m2 * R(1.0 / 36.0);
-    R a3 = m3 * R(1.0 / 6.0), a4 = m4 * R(1.0 / 12.0), a5 = m5 * R(1.0 / 6.0);
-    R a6 = m6 * R(1.0 / 12.0), a7 = m7 * R(0.25), a8 = m8 * R(0.25);
-    R axis = a0 - a1 - R(2) * a2;
-    R diag = a0 + R(2) * a1 + a2;
-    R px = a3 - R(2) * a4, py = a5 - R(2) * a6;
-    R qx = a3 + a4, qy = a5 + a6;
-    f[0] = a0 - R(4) * a1 + R(4) * a2;
-    f[1] = axis + px + a7;
-    f[2] = axis + py - a7;
-    f[3] = axis - px + a7;
-    f[4] = axis - py - a7;
-    f[5] = diag + qx + qy + a8;
-    f[6] = diag - qx + qy - a8;
-    f[7] = diag - qx - qy + a8;
-    f[8] = diag + qx - qy - a8;
+    const R u2e = (ux * ux + uy * uy) * ie;
+    const R uF = (ux * Fx + uy * Fy) * ie;
+    const R e1 = R(-2) * rho + R(3) * u2e;
+    const R e2 = rho - R(3) * u2e;
+    const R e7 = (ux * ux - uy * uy) * ie;
+    const R e8 = ux * uy * ie;
+    const R S1 = R(6) * uF;
+    const R S7 = R(2) * (ux * Fx - uy * Fy) * ie;
+    const R S8 = (ux * Fy + uy * Fx) * ie;
+    // Lambda (m - m_eq) - (I - Lambda/2) S, component by component (S_2 = -S_1, S_4 = -F_x, ...)
+    const R d1 = c.s1 * (m1 - e1) - (R(1) - R(0.5) * c.s1) * S1;
+    const R d2 = c.s2 * (m2 - e2) + (R(1) - R(0.5) * c.s2) * S1;
+    const R d3 = c.s3 * (m3 - ux) - (R(1) - R(0.5) * c.s3) * Fx;
+    const R d4 = c.s4 * (m4 + ux) + (R(1) - R(0.5) * c.s4) * Fx;
+    const R d5 = c.s5 * (m5 - uy) - (R(1) - R(0.5) * c.s5) * Fy;
+    const R d6 = c.s6 * (m6 + uy) + (R(1) - R(0.5) * c.s6) * Fy;
+    const R d7 = c.s7 * (m7 - e7) - (R(1) - R(0.5) * c.s7) * S7;
+    const R d8 = c.s8 * (m8 - e8) - (R(1) - R(0.5) * c.s8) * S8;
+    // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+    const R a1 = d1 * R(1.0 / 36.0), a2 = d2 * R(1.0 / 36.0);
+    const R a3 = d3 * R(1.0 / 6.0), a4 = d4 * R(1.0 / 12.0);
+    const R a5 = d5 * R(1.0 / 6.0), a6 = d6 * R(1.0 / 12.0);
+    const R a7 = d7 * R(0.25), a8 = d8 * R(0.25);
+    const R axis = -a1 - R(2) * a2;
+    const R diag = R(2) * a1 + a2;
+    const R px = a3 - R(2) * a4, py = a5 - R(2) * a6;
+    const R qx = a3 + a4, qy = a5 + a6;
+    f[0] -= R(4) * (a2 - a1);
+    f[1] -= axis + px + a7;
+    f[2] -= axis + py - a7;
+    f[3] -= axis - px + a7;
+    f[4] -= axis - py - a7;
+    f[5] -= diag + qx + qy + a8;
+    f[6] -= diag - qx + qy - a8;
+    f[7] -= diag - qx - qy + a8;
+    f[8] -= diag + qx - qy - a8;
     // Eq. 27 with d(Phi u)/dt = (Phi u)|t - (Phi u)|t-1 (Sec. 3.2)
-    R T = c.T0 + M.Tp, C = c.C0 + M.Cp;
-    R Tux = T * ux, Tuy = T * uy, Cux = C * ux, Cuy = C * uy;
-    R XTx = Tux - hist[0], XTy = Tuy - hist[1], XCx = Cux - hist[2], XCy = Cuy - hist[3];
+    const R T = c.T0 + M.Tp, C = c.C0 + M.Cp;
+    const R Tux = T * ux, Tuy = T * uy, Cux = C * ux, Cuy = C * uy;
+    const R XTx = Tux - hist[0], XTy = Tuy - hist[1], XCx = Cux - hist[2], XCy = Cuy - hist[3];
     hist[0] = Tux;
     hist[1] = Tuy;
     hist[2] = Cux;

@@ -34,11 +34,16 @@ def make_pair(O, spec: CavitySpec, precision="f64", layout="ab", **kw):
     return gpu, ora
 
 
-def compare(gpu, ora, tol, nush_tol=None):
+def compare(gpu, ora, tol, nush_tol=None, u_atol=0.0):
+    """Relative L2 error of u, T, C within tol.  u_atol admits an absolute error
+    on u for states where u is so small that the unshifted FP64 oracle's own
+    rounding (about 1e-17 absolute on sums of O(0.1) populations) dominates."""
     fg = gpu.fields()
     fo = ora.fields()
     errs = {k: rel_l2(fg[k], fo[k]) for k in KEYS}
     for k in KEYS:
+        if k in ("ux", "uy") and np.abs(fg[k] - fo[k]).max() <= u_atol:
+            continue
         assert errs[k] <= tol, (k, errs)
     assert np.abs(fg["rho"] - fo["rho"]).max() <= 1e3 * tol
     if nush_tol is not None:
@@ -64,7 +69,7 @@ def test_first_steps_f64(oracle_mod, layout, nsteps):
     gpu.step(nsteps)
     ora.step(nsteps)
     assert gpu.t == nsteps
-    compare(gpu, ora, 1e-13, nush_tol=1e-13)
+    compare(gpu, ora, 1e-13, nush_tol=1e-13, u_atol=1e-15)
 
 
 @pytest.mark.parametrize("layout", ["ab", "aa"])
@@ -158,14 +163,22 @@ def test_user_initial_fields_match_oracle(oracle_mod):
 def test_residual_and_divergence_flag():
     spec = SMALL_AIDING
     g = lbm.Cavity(*spec.args(), precision="f32", seed=1)
-    assert g.residual() == float("inf")
-    g.step(100)
+    assert g.residual() == float("inf")     # no snapshot yet
+    g.step(5000)
     r1 = g.residual()
-    assert 0 < r1 < 1
-    p = lbm.lbm_derive_params(16, 16, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
-    p.gbT = 50.0   # absurd buoyancy: the state blows up to non-finite values
-    bad = lbm.Cavity(params=p, precision="f32", noise=0.1)
-    bad.step(2000)
+    g.step(100)
+    r2 = g.residual()
+    assert 0 < r2 < 0.1 and r2 < r1
+    # a non-finite initial value (made on the host) must be reported, not propagated silently
+    T = np.full((16, 16), 0.5)
+    T[8, 8] = np.nan
+    bad = lbm.Cavity(16, 16, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0, precision="f32", T_init=T,
+                     C_init=np.full((16, 16), 0.5))
+    bad.step(50)
     with pytest.raises(lbm.LbmError) as ei:
         bad.residual()
+    assert ei.value.status == lbm.ERR_DIVERGED
+    bad.step(200)
+    with pytest.raises(lbm.LbmError) as ei:
+        bad.nusselt_sherwood()
     assert ei.value.status == lbm.ERR_DIVERGED
