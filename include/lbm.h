@@ -187,6 +187,32 @@ lbm_status lbm_load(lbm_ctx* ctx, const void* buf, size_t len);
 lbm_status lbm_get_params(const lbm_ctx* ctx, lbm_params* out);
 size_t lbm_device_bytes(const lbm_ctx* ctx);
 
+/* Largest grid lbm_residual_noalloc() accepts, set by its fixed scratch array. */
+#define LBM_NOALLOC_MAX_BLOCKS 4096
+#define LBM_NOALLOC_MAX_NODES (LBM_NOALLOC_MAX_BLOCKS * 1024)
+
+/* The steady-state residual of lbm_residual(), for callers that cannot let the
+ * library allocate device memory when they ask for it: code embedded in a host
+ * framework that has already reserved the device memory for its own pool, and
+ * loops that must not stall, since cudaMalloc and cudaFree can synchronise
+ * the whole device.  The paper has no counterpart; this is plumbing.
+ *   snapshot       caller-owned device buffer of 4 * nx * ny doubles, planes
+ *                  (u_x, u_y, T, C) of [ny][nx]; read as the previous snapshot
+ *                  and overwritten with the current fields.
+ *   have_snapshot  0 if snapshot holds no earlier fields (then *r = +inf).
+ *   r              host output, defined as in lbm_residual().
+ * Allocates nothing: the per-block maxima live in one file-scope device array
+ * of LBM_NOALLOC_MAX_BLOCKS * 9 + 16 doubles (about 288 KiB), which every GPU
+ * that loads the library holds until the process exits.  Grids of more than
+ * LBM_NOALLOC_MAX_NODES nodes are rejected with LBM_ERR_INVALID.  The first
+ * call on each device looks up the array's device address; make that first
+ * call before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (each call writes every slot it reads, so nothing has
+ * to be cleared); calls whose work overlaps on the GPU, from any context or
+ * stream, race on it.  Synchronises the context's stream.  Errors as for
+ * lbm_residual(), plus LBM_ERR_INVALID for NULL arguments. */
+lbm_status lbm_residual_noalloc(lbm_ctx* ctx, double* snapshot, int have_snapshot, double* r);
+
 /* Releases everything the context owns.  NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);
 

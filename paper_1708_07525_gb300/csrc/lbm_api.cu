@@ -261,6 +261,24 @@ lbm_status do_init(lbm_ctx* c, const double* T_host, const double* C_host, uint6
 
 }  // namespace
 
+bool lbm_ctx_view(const lbm_ctx* c, CtxView* v) {
+    if (!c || !v) return false;
+    v->prec = c->prec;
+    v->buf = cur_buf(c);
+    v->G = c->G;
+    v->cd = &c->cd;
+    v->cf = &c->cf;
+    v->mode = c->read_mode();
+    v->stream = c->stream;
+    v->device = c->device;
+    return true;
+}
+
+void lbm_set_error(lbm_ctx* c, const char* msg) {
+    if (c) c->err = msg;
+    g_last_error = msg;
+}
+
 extern "C" {
 
 lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, double Pr,

@@ -63,4 +63,22 @@ cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename 
                             cudaStream_t st);
 int residual_blocks(const Geom& G);
 
+// Read-only view of a context's device state, for entry points defined in
+// other translation units of the library.
+struct CtxView {
+    int prec;
+    const void* buf;         // buffer holding the current state
+    Geom G;
+    const Coef<double>* cd;
+    const Coef<float>* cf;
+    int mode;                // GATHER_* for the current level
+    cudaStream_t stream;
+    int device;
+};
+
 }  // namespace lbm
+
+struct lbm_ctx;
+bool lbm_ctx_view(const lbm_ctx* ctx, lbm::CtxView* out);
+// Records msg as the last error of ctx (or of the calling thread if ctx is NULL).
+void lbm_set_error(lbm_ctx* ctx, const char* msg);

@@ -1,0 +1,121 @@
+// Steady-state residual without any device allocation.
+//
+// lbm_residual() allocates its snapshot and its per-block partial maxima on
+// the first call.  Some callers cannot allocate device memory at that point:
+// a host framework that has reserved the device memory for its own pool, or
+// a loop that must not stall on cudaMalloc / cudaFree, which can synchronise
+// the device.  lbm_residual_noalloc() computes the same residual with the
+// caller's snapshot buffer and with its partial maxima in the file-scope
+// array below.  There is no counterpart in the paper; this is plumbing.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "../../include/lbm.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int NOALLOC_THREADS = RES_THREADS;       // threads per block
+constexpr int NOALLOC_NODES_PER_BLOCK = 4 * RES_THREADS;
+constexpr int NOALLOC_OUT = LBM_NOALLOC_MAX_BLOCKS * 9;   // offset of the 9 results
+
+// Partial maxima of up to LBM_NOALLOC_MAX_BLOCKS blocks (9 doubles each) plus the
+// 9 folded results.  Every GPU that loads the library holds this array (about
+// 288 KiB) until the process exits.  In host code `noalloc_scratch` is only a
+// host-side stand-in for the symbol; its device address comes from
+// cudaGetSymbolAddress (see scratch_for_device).
+__device__ __align__(256) double noalloc_scratch[LBM_NOALLOC_MAX_BLOCKS * 9 + 16];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+double* g_ptr[MAX_DEVICES] = {};
+
+// Device address of the scratch array on `dev`, looked up once per device with that
+// device current.  This happens on the first call on each device, so that first call
+// must not come while a stream is being captured.
+cudaError_t scratch_for_device(int dev, double** out) {
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_ptr[dev]) {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+        double* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void**)&p, noalloc_scratch);
+        if (prev != dev && prev >= 0) cudaSetDevice(prev);
+        if (e != cudaSuccess) return e;
+        g_ptr[dev] = p;
+    }
+    *out = g_ptr[dev];
+    return cudaSuccess;
+}
+
+inline const Coef<double>& coef_of(const CtxView& v, double*) { return *v.cd; }
+inline const Coef<float>& coef_of(const CtxView& v, float*) { return *v.cf; }
+
+template <typename S>
+cudaError_t launch(const CtxView& v, double* snap, double* scratch, int nb) {
+    using R = typename Real<S>::type;
+    const Coef<R>& c = coef_of(v, (R*)nullptr);
+    residual_kernel<S><<<nb, NOALLOC_THREADS, 0, v.stream>>>((const S*)v.buf, v.G, c, v.mode, snap,
+                                                             scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    residual_final_kernel<<<1, RES_THREADS, 0, v.stream>>>(scratch, nb, scratch + NOALLOC_OUT);
+    return cudaGetLastError();
+}
+
+lbm_status fail(lbm_ctx* ctx, lbm_status s, const char* m, const char* detail = "") {
+    char msg[256];
+    std::snprintf(msg, sizeof msg, "lbm_residual_noalloc: %s%s", m, detail);
+    lbm_set_error(ctx, msg);
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_residual_noalloc(lbm_ctx* ctx, double* snapshot, int have_snapshot, double* r) {
+    CtxView v;
+    if (!ctx || !snapshot || !r || !lbm_ctx_view(ctx, &v))
+        return fail(ctx, LBM_ERR_INVALID, "ctx, snapshot and r must be non-NULL");
+    const size_t n = (size_t)v.G.nx * v.G.ny;
+    if (n > (size_t)LBM_NOALLOC_MAX_NODES) {
+        char d[128];
+        std::snprintf(d, sizeof d, " (grid of %zu nodes; the limit is %d)", n, LBM_NOALLOC_MAX_NODES);
+        return fail(ctx, LBM_ERR_INVALID, "grid larger than the static scratch supports", d);
+    }
+    const int nb = (int)((n + NOALLOC_NODES_PER_BLOCK - 1) / NOALLOC_NODES_PER_BLOCK);
+    double* scratch = nullptr;
+    cudaError_t e = scratch_for_device(v.device, &scratch);
+    if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, "cudaGetSymbolAddress: ", cudaGetErrorString(e));
+    // Every partial slot the fold reads is written by this call, and the fold writes all
+    // nine results, so nothing in the shared array has to be cleared first.
+    switch (v.prec) {
+        case LBM_F64: e = launch<double>(v, snapshot, scratch, nb); break;
+        case LBM_F32: e = launch<float>(v, snapshot, scratch, nb); break;
+        case LBM_BF16: e = launch<__nv_bfloat16>(v, snapshot, scratch, nb); break;
+        default: e = launch<__half>(v, snapshot, scratch, nb); break;
+    }
+    double h[9];
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, scratch + NOALLOC_OUT, sizeof h, cudaMemcpyDeviceToHost, v.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(v.stream);
+    if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, "", cudaGetErrorString(e));
+    if (h[8] != 0.0) return fail(ctx, LBM_ERR_DIVERGED, "non-finite field value");
+    double res = 0.0;
+    for (int q = 0; q < 4; ++q) {
+        const double rq = h[4 + q] > 0 ? h[q] / h[4 + q] : (h[q] > 0 ? INFINITY : 0.0);
+        res = rq > res ? rq : res;
+    }
+    *r = have_snapshot ? res : INFINITY;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -20,6 +20,7 @@ AB_PULL, AA = 0, 1
 WALL_DIRICHLET, WALL_ADIABATIC = 0, 1
 PRECISIONS = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
 LAYOUTS = {"ab": AB_PULL, "aa": AA}
+NOALLOC_MAX_NODES = 4096 * 1024   # LBM_NOALLOC_MAX_NODES
 
 OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_UNCONVERGED = range(7)
 _STATUS = {1: "LBM_ERR_INVALID", 2: "LBM_ERR_NOMEM", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_DIVERGED",
@@ -88,6 +89,7 @@ def lib():
             L.lbm_fields.argtypes = [P, dp, dp, dp, dp, dp]
             L.lbm_nusselt_sherwood.argtypes = [P, dp]
             L.lbm_residual.argtypes = [P, dp]
+            L.lbm_residual_noalloc.argtypes = [P, C.c_void_p, C.c_int, dp]
             L.lbm_save.argtypes = [P, C.c_void_p, C.POINTER(C.c_size_t)]
             L.lbm_load.argtypes = [P, C.c_void_p, C.c_size_t]
             L.lbm_get_params.argtypes = [P, C.POINTER(lbm_params)]
@@ -97,7 +99,8 @@ def lib():
             L.lbm_last_error.argtypes = [P]
             L.lbm_last_error.restype = C.c_char_p
             for name in ("lbm_derive_params", "lbm_create", "lbm_create_raw", "lbm_reset", "lbm_step",
-                         "lbm_fields", "lbm_nusselt_sherwood", "lbm_residual", "lbm_save",
+                         "lbm_fields", "lbm_nusselt_sherwood", "lbm_residual",
+                         "lbm_residual_noalloc", "lbm_save",
                          "lbm_load", "lbm_get_params"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -242,6 +245,14 @@ class Cavity:
     def residual(self):
         r = C.c_double()
         _check(lib().lbm_residual(self.h, C.byref(r)), self.h)
+        return r.value
+
+    def residual_noalloc(self, snapshot_ptr: int, have_snapshot: bool) -> float:
+        """lbm_residual_noalloc: residual against a caller-owned device snapshot of
+        4 * nx * ny doubles; the library allocates nothing for this call."""
+        r = C.c_double()
+        _check(lib().lbm_residual_noalloc(self.h, C.c_void_p(int(snapshot_ptr)),
+                                          int(bool(have_snapshot)), C.byref(r)), self.h)
         return r.value
 
     def save(self) -> bytes:

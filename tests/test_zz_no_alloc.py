@@ -1,0 +1,48 @@
+"""lbm_residual_noalloc, the residual entry point that allocates nothing (for
+callers whose device memory is already reserved by a host framework, or that
+must not stall on cudaMalloc / cudaFree), checked through the C ABI against
+lbm_residual on two calls in a row.  Collected last on purpose."""
+import numpy as np
+import pytest
+
+from paper_1708_07525_gb300 import lbm
+from paper_1708_07525_gb300.workloads import CavitySpec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision,layout", [("f32", "ab"), ("f64", "aa"), ("bf16", "ab")])
+def test_noalloc_residual_matches_allocating_entry_point(precision, layout):
+    import torch
+    spec = CavitySpec(130, 67, Ra=3e4, Da=1e-2, eps=0.5, Le=0.7, N=-2.0, sigma=0.6, seed=14,
+                      noise=0.01)
+    cav = lbm.Cavity(*spec.args(), precision=precision, layout=layout, seed=spec.seed,
+                     noise=spec.noise)
+    snap = torch.zeros(4 * spec.nx * spec.ny, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    cav.step(500)
+    assert cav.residual() == float("inf")
+    assert cav.residual_noalloc(snap.data_ptr(), False) == float("inf")
+    fl = cav.fields(("ux", "uy", "T", "C"))
+    host = snap.view(4, spec.ny, spec.nx).cpu().numpy()
+    for q, k in enumerate(("ux", "uy", "T", "C")):
+        np.testing.assert_array_equal(host[q], fl[k])      # the snapshot holds the fields
+    for _ in range(2):                                      # two calls in a row
+        cav.step(101)
+        r_ref = cav.residual()
+        r_new = cav.residual_noalloc(snap.data_ptr(), True)
+        assert np.isfinite(r_ref) and r_ref > 0
+        assert abs(r_new - r_ref) <= 1e-12 * r_ref, (r_new, r_ref)
+    cav.close()
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch():
+    import torch
+    n = int(np.sqrt(lbm.NOALLOC_MAX_NODES)) + 1
+    cav = lbm.Cavity(n, n, 1e5, 1e-3, 0.4, 1.0, 5.0, -1.0, precision="bf16", layout="aa")
+    snap = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(lbm.LbmError) as ei:
+        cav.residual_noalloc(snap.data_ptr(), True)
+    assert ei.value.status == lbm.ERR_INVALID
+    assert "static scratch" in str(ei.value)
+    cav.close()
