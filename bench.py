@@ -324,6 +324,170 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Many uneven cavities (grids drawn from 32^2..256^2, parameters drawn from the
+    mixed ranges) advanced together: one fused launch per L2-sized group per step,
+    autotuned tiles, CUDA graphs; aggregate GLUPS against one launch per cavity."""
+    import numpy as np
+    import torch
+    from paper_1708_07525_gb300 import lbm
+    from paper_1708_07525_gb300.workloads import draw_batch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    specs = draw_batch(args.count, seed=4)
+    insts = [lbm.make_instance(s) for s in specs]
+    nodes = sum(s.nx * s.ny for s in specs)
+    b = lbm.Batch(insts, precision=args.precision, layout=args.layout, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    report = b.autotune(trial_steps=16)
+    tune_s = time.perf_counter() - t0
+    b.step(64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        b.step(args.batch_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    glups = nodes * args.batch_steps / (ms / 1e3) / 1e9
+    nush = b.nusselt_sherwood()
+    b.close()
+    # one launch per cavity per step, on one stream
+    cavs = [lbm.Cavity(*s.args(), varpi=s.varpi, precision=args.precision, layout=args.layout,
+                       seed=s.seed, noise=s.noise, stream=stream.cuda_stream, graph_chunk=-1)
+            for s in specs]
+    k = max(2, args.batch_steps // 50)
+    for c in cavs:
+        c.step(2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k):
+        for c in cavs:
+            c.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_ms = e0.elapsed_time(e1)
+    per_glups = nodes * k / (per_ms / 1e3) / 1e9
+    del cavs
+    line = {
+        "metric": METRIC, "mode": "batch", "value": glups, "unit": "GLUPS", "n_gpus": 1,
+        "steps": args.batch_steps, "higher_is_better": True, "dtype": args.precision,
+        "data": "synthetic",
+        "config": {"workload": f"{args.count} cavities, grids 32^2-256^2 drawn by seed 4, "
+                               f"log-uniform Ra in [1e3,1e5], Da in [1e-4,1e-1], uniform eps, Le, N, "
+                               f"sigma; {args.precision} {args.layout}",
+                   "nodes": nodes, "time_steps": args.batch_steps},
+        "one_launch_per_cavity_glups": per_glups,
+        "speedup_vs_one_launch_per_cavity": glups / per_glups,
+        "autotune_s": tune_s, "autotune": report.strip().splitlines(),
+        "clocks": clk.summary(),
+        "finite_nush": int(np.isfinite(nush).all(axis=1).sum()),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Continuous-batching solver service against plain one-at-a-time FP64 solves.
+    Requests: grids from `--serve-sizes`, parameters from the mixed ranges, Poisson
+    arrivals at 0.8 x the service capacity measured on a burst of the same requests."""
+    import numpy as np
+    import torch
+    from paper_1708_07525_gb300 import lbm
+    from paper_1708_07525_gb300.workloads import draw_batch, arrivals
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sizes = tuple(int(x) for x in args.serve_sizes.split(","))
+    specs = draw_batch(args.requests, seed=5, sizes=sizes)
+    insts = [lbm.make_instance(s) for s in specs]
+    cap_steps = args.max_steps
+    check = args.check_every
+
+    def serve(arrive):
+        srv = lbm.Server(args.budget_gb * (1 << 30), max_slots=len(specs), check_every=check,
+                         precision=args.precision, layout=args.layout, stream=stream.cuda_stream)
+        t_start = time.perf_counter()
+        pending = list(range(len(specs)))
+        submitted_at = {}
+        done = {}
+        while len(done) < len(specs):
+            now = time.perf_counter() - t_start
+            while pending and arrive[pending[0]] <= now:
+                k = pending.pop(0)
+                srv.submit(insts[k], tol=args.serve_tol, nush_tol=args.nush_tol,
+                           max_steps=cap_steps, rid=k)
+                submitted_at[k] = now
+            active = srv.tick()
+            t_now = time.perf_counter() - t_start
+            for r in srv.poll():
+                done[r["id"]] = dict(r, arrival=arrive[r["id"]], finished=t_now)
+            if active == 0 and pending and srv.info()["queued"] == 0:
+                time.sleep(max(0.0, arrive[pending[0]] - (time.perf_counter() - t_start)))
+        makespan = time.perf_counter() - t_start
+        srv.close()
+        return done, makespan
+
+    burst, burst_s = serve(np.zeros(len(specs)))
+    capacity = len(specs) / burst_s
+    arr = arrivals(len(specs), 0.8 * capacity, seed=5)
+    arr = arr - arr[0]
+    served, served_s = serve(arr)
+    lat = np.array([served[k]["finished"] - served[k]["arrival"] for k in served])
+
+    # plain path: one FP64 cavity at a time, same check interval, residual < fp64_tol
+    plain = {}
+    t0 = time.perf_counter()
+    for k, s in enumerate(specs):
+        if time.perf_counter() - t0 > args.plain_budget_s:
+            break
+        c = lbm.Cavity(*s.args(), varpi=s.varpi, precision="f64", seed=s.seed, noise=s.noise,
+                       stream=stream.cuda_stream)
+        status, steps = "unconverged", 0
+        c.residual()
+        while steps < cap_steps:
+            c.step(check)
+            steps += check
+            if c.residual() < args.fp64_tol:
+                status = "ok"
+                break
+        plain[k] = {"nush": c.nusselt_sherwood().tolist(), "steps": steps, "status": status}
+        c.close()
+    plain_s = time.perf_counter() - t0
+    errs = []
+    for k, p in plain.items():
+        if p["status"] == "ok" and served[k]["status"] == 0:
+            a, b = np.array(served[k]["nush"]), np.array(p["nush"])
+            errs.append(float(np.max(np.abs(a - b) / np.abs(b))))
+    errs = np.array(errs) if errs else np.array([np.nan])
+    statuses = [served[k]["status"] for k in served]
+    line = {
+        "metric": METRIC, "mode": "serve", "value": len(specs) / served_s, "unit": "solves/s",
+        "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"{len(specs)} cavity solve requests, grids {sizes}, parameters "
+                               f"from the mixed ranges (seed 5), Poisson arrivals at 0.8 x burst "
+                               f"capacity; steady when residual < {args.serve_tol} or Nu/Sh change "
+                               f"< {args.nush_tol} per {check} steps; cap {cap_steps} steps",
+                   "precision": args.precision, "budget_gb": args.budget_gb},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(lat.max())},
+        "burst_capacity_solves_per_s": capacity,
+        "served_status": {"ok": statuses.count(0), "unconverged": statuses.count(6),
+                          "diverged": statuses.count(4)},
+        "plain_fp64": {"solves": len(plain), "solves_per_s": len(plain) / plain_s,
+                       "converged": sum(p["status"] == "ok" for p in plain.values()),
+                       "tol": args.fp64_tol},
+        "speedup_vs_plain_fp64": (len(specs) / served_s) / (len(plain) / plain_s),
+        "nush_rel_err_vs_fp64": {"n": int(np.isfinite(errs).sum()),
+                                 "max": float(np.nanmax(errs)), "median": float(np.nanmedian(errs)),
+                                 "frac_le_1e-3": float(np.mean(errs <= 1e-3))},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,7 +502,23 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"])
+    ap.add_argument("--count", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=5000)
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--serve-sizes", default="64,128")
+    ap.add_argument("--serve-tol", type=float, default=1e-6)
+    ap.add_argument("--nush-tol", type=float, default=0.0)
+    ap.add_argument("--fp64-tol", type=float, default=1e-7)
+    ap.add_argument("--check-every", type=int, default=500)
+    ap.add_argument("--max-steps", type=int, default=300000)
+    ap.add_argument("--budget-gb", type=float, default=8.0)
+    ap.add_argument("--plain-budget-s", type=float, default=120.0)
     args = ap.parse_args()
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

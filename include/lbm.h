@@ -90,6 +90,10 @@ typedef struct {
     void* alloc_user;
     int block_x, block_y;       /* launch tile of the step kernel; 0 -> tuned default */
     int graph_chunk;            /* steps per captured CUDA graph; 0 -> default, <0 -> off */
+    int round_nearest;          /* 16-bit storage: 0 (default) -> stochastic rounding of every
+                                   stored population (unbiased; random bits hashed from the
+                                   node index and its pre-collision state, so runs are
+                                   reproducible); 1 -> round to nearest even */
 } lbm_options;
 
 /* Derived lattice constants (Sec. 4 / 4.1 mapping).  Filled by
@@ -186,6 +190,134 @@ lbm_status lbm_load(lbm_ctx* ctx, const void* buf, size_t len);
 /* Parameters in use, and bytes of device memory the context holds. */
 lbm_status lbm_get_params(const lbm_ctx* ctx, lbm_params* out);
 size_t lbm_device_bytes(const lbm_ctx* ctx);
+
+/* ---- Many cavities in one launch ------------------------------------------
+ * A batch holds cavities of different sizes and parameters in one device arena
+ * and advances all of them with one fused launch per time step (the same
+ * per-node work as lbm_step: Sec. 3, Eqs. 5-27), tiled per cavity and captured
+ * in CUDA graphs.  All cavities of a batch share the storage precision and the
+ * memory pattern given in lbm_options; the per-cavity noise seed and amplitude
+ * come from the descriptors.  Results of a cavity do not depend on the other
+ * members of the batch (bitwise). */
+typedef struct lbm_batch lbm_batch;
+
+typedef struct {
+    lbm_params params;          /* from lbm_derive_params() or written by the caller */
+    uint64_t seed;              /* initial-noise seed of this cavity */
+    double noise;               /* noise amplitude (<0 none, 0 -> 1e-3) */
+} lbm_instance;
+
+/* Create a batch with room for `capacity` cavities in a device arena of
+ * `arena_bytes` (0 -> exactly what the `count` initial cavities need; then
+ * nothing more can be added).  The first `count` cavities of `inst` (may be 0)
+ * are added at t = 0.  Errors: LBM_ERR_INVALID, LBM_ERR_NOMEM, LBM_ERR_CUDA. */
+lbm_status lbm_batch_create(const lbm_instance* inst, int count, int capacity,
+                            size_t arena_bytes, const lbm_options* opt, lbm_batch** out);
+
+/* Bytes of arena one cavity of this grid needs in a batch with these options. */
+size_t lbm_batch_instance_bytes(lbm_grid grid, const lbm_options* opt);
+
+/* Add one cavity at the batch's current time; *slot receives its index.
+ * LBM_ERR_NOMEM if no free slot or no arena block is large enough (the arena is
+ * the admission budget). */
+lbm_status lbm_batch_add(lbm_batch* b, const lbm_instance* inst, int* slot);
+
+/* Remove a cavity and return its arena block; its slot becomes free. */
+lbm_status lbm_batch_remove(lbm_batch* b, int slot);
+
+/* Advance every cavity of the batch by n time steps (asynchronous). */
+lbm_status lbm_batch_step(lbm_batch* b, int64_t n);
+
+/* Steps taken by the cavity in `slot` since it was added (-1 if the slot is free). */
+int64_t lbm_batch_time(const lbm_batch* b, int slot);
+
+/* Mean Nu/Sh (Eq. 38) of every slot: out[4 * slot + k] as in lbm_nusselt_sherwood
+ * (zeros for free slots); out has 4 * capacity doubles.  Synchronises. */
+lbm_status lbm_batch_nusselt_sherwood(lbm_batch* b, double* out);
+
+/* Residual (as lbm_residual) of every slot against its previous call: r has
+ * `capacity` doubles (+inf on a cavity's first call, 0 for free slots);
+ * diverged[slot] (may be NULL) is set to 1 for cavities with non-finite values.
+ * Synchronises. */
+lbm_status lbm_batch_residual(lbm_batch* b, double* r, int* diverged);
+
+/* Fields of one cavity, as lbm_fields.  Synchronises. */
+lbm_status lbm_batch_fields(lbm_batch* b, int slot, double* ux, double* uy, double* T, double* C,
+                            double* rho);
+
+/* Choose the tile shape of every grid size present in the batch by timing
+ * candidate shapes (widths 32-256, heights 1-16) over `trial_steps` steps on
+ * scratch cavities of that size (the batch's own state is not touched), and
+ * apply them.  The choice is cached per (nx, ny, precision, layout) for the
+ * process and used by later batches.  report (may be NULL, `cap` chars)
+ * receives one line per size: "nx ny tile_w tile_h us_per_step". */
+lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, char* report, size_t cap);
+
+/* Set the tile shape of one cavity by hand (tile_w a power of two in 32..256,
+ * tile_h >= 1, tile_w * tile_h <= 4096).  Results do not depend on it. */
+lbm_status lbm_batch_set_tile(lbm_batch* b, int slot, int tile_w, int tile_h);
+
+/* L2 temporal blocking: cavities are grouped so that a group's per-step working
+ * set stays within l2_bytes (0 -> keep; default half the L2), and each group is
+ * advanced `steps` steps (default 16) before the next, so that its state is read
+ * from L2 rather than HBM on all but the first of them.  steps = 1 turns it off.
+ * Results do not depend on it. */
+lbm_status lbm_batch_set_blocking(lbm_batch* b, int steps, size_t l2_bytes);
+
+/* Number of slots, slots in use, and the arena size / bytes in use. */
+lbm_status lbm_batch_info(const lbm_batch* b, int* capacity, int* used, size_t* arena_bytes,
+                          size_t* arena_used);
+
+void lbm_batch_destroy(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* ---- Serving: cavity solves as requests ------------------------------------
+ * A server keeps a batch whose arena is the device-memory budget.  Submitted
+ * requests wait in a FIFO queue; every tick admits the queued requests whose
+ * storage fits in the arena (later requests may fill space an earlier, larger
+ * one cannot use), advances every admitted cavity by `check_every` steps with
+ * the batch's fused launch, computes each one's residual (lbm_residual), and
+ * retires those below their tolerance (status LBM_OK), past their step cap
+ * (LBM_ERR_UNCONVERGED) or non-finite (LBM_ERR_DIVERGED), freeing their
+ * storage for the next admissions.  Because a cavity's work does not depend
+ * on the rest of the batch and checks fall every `check_every` steps after
+ * admission, a request's result is the same whatever it was served with. */
+typedef struct lbm_server lbm_server;
+
+typedef struct {
+    int64_t id;                 /* the caller's request id */
+    int status;                 /* LBM_OK, LBM_ERR_UNCONVERGED or LBM_ERR_DIVERGED */
+    int64_t steps;              /* time steps taken */
+    double residual;            /* last residual */
+    double nush[4];             /* Nu_L, Sh_L, Nu_R, Sh_R at the end (Eq. 38) */
+    double t_submit, t_admit, t_done;   /* seconds on the server clock */
+} lbm_result;
+
+/* budget_bytes: device arena for the cavities' storage; max_slots: cavities in
+ * flight at most; check_every: steps per tick (even, >= 2).  Precision, memory
+ * pattern, stream and allocator come from opt (FP32, BF16 or FP16 storage). */
+lbm_status lbm_server_create(size_t budget_bytes, int max_slots, int check_every,
+                             const lbm_options* opt, lbm_server** out);
+/* Queue one solve.  It is steady (status LBM_OK) at the first check where the
+ * residual over the last check_every steps is below tol (tol > 0), or where every
+ * one of Nu_L, Sh_L, Nu_R, Sh_R changed by less than nush_tol relative to its
+ * value since the previous check (nush_tol > 0; the Nu/Sh rule averages over a
+ * wall and so tolerates the rounding noise of 16-bit storage, which keeps the
+ * field residual near 1e-3); else it stops after max_steps steps. */
+lbm_status lbm_server_submit(lbm_server* s, const lbm_instance* inst, double tol,
+                             double nush_tol, int64_t max_steps, int64_t id);
+/* One tick (admit, step, check, retire); *active receives the cavities in flight
+ * afterwards (may be NULL).  Synchronises the stream. */
+lbm_status lbm_server_tick(lbm_server* s, int* active);
+/* Move up to cap finished results to out; *n receives how many. */
+lbm_status lbm_server_poll(lbm_server* s, lbm_result* out, int cap, int* n);
+/* Seconds since the server was created (the clock of lbm_result). */
+double lbm_server_clock(const lbm_server* s);
+/* Queue length, cavities in flight, results not yet polled, arena bytes in use. */
+lbm_status lbm_server_info(const lbm_server* s, int* queued, int* active, int* done,
+                           size_t* arena_used);
+void lbm_server_destroy(lbm_server* s);
+const char* lbm_server_last_error(const lbm_server* s);
 
 /* Largest grid lbm_residual_noalloc() accepts, set by its fixed scratch array. */
 #define LBM_NOALLOC_MAX_BLOCKS 4096

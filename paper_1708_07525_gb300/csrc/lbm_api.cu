@@ -35,6 +35,10 @@ size_t storage_size(int prec) {
     }
 }
 
+
+}  // namespace
+
+namespace lbm {
 template <typename R>
 Coef<R> make_coef(const lbm_params& P) {
     Coef<R> c;
@@ -71,8 +75,14 @@ Coef<R> make_coef(const lbm_params& P) {
     }
     c.dirichlet_mask = (P.wall_lr == LBM_WALL_DIRICHLET ? 3 : 0) |
                        (P.wall_tb == LBM_WALL_DIRICHLET ? 12 : 0);
+    c.sr = 1;
     return c;
 }
+template Coef<float> make_coef<float>(const lbm_params&);
+template Coef<double> make_coef<double>(const lbm_params&);
+}  // namespace lbm
+
+namespace {
 
 bool rate_ok(double s) { return s > 0.0 && s < 2.0; }
 
@@ -118,6 +128,7 @@ struct lbm_ctx {
     Coef<float> cf{};
     LaunchCfg L{};
     int graph_chunk = 0;
+    bool round_nearest = false;     // 16-bit storage: nearest-even instead of stochastic
     cudaGraphExec_t graph = nullptr;
     lbm_alloc_fn alloc = nullptr;
     lbm_free_fn free_fn = nullptr;
@@ -409,6 +420,8 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
     c->G.plane = (size_t)ny * c->G.pitch;
     c->cd = make_coef<double>(c->P);
     c->cf = make_coef<float>(c->P);
+    c->round_nearest = O.round_nearest != 0;
+    c->cf.sr = c->round_nearest ? 0 : 1;
     int bx = O.block_x, by = O.block_y;
     if (bx == 0) bx = nx >= 128 ? 128 : 32;
     if (by == 0) by = bx >= 128 ? 1 : 128 / bx;
@@ -689,6 +702,7 @@ lbm_status lbm_load(lbm_ctx* c, const void* buf, size_t len) {
     c->P = h.P;
     c->cd = make_coef<double>(c->P);
     c->cf = make_coef<float>(c->P);
+    c->cf.sr = c->round_nearest ? 0 : 1;
     if (c->graph) {   // constants are baked into the captured launches
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;

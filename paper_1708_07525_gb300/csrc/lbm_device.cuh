@@ -34,23 +34,80 @@ static_assert(opp_of(5) == 7 && opp_of(7) == 5 && opp_of(6) == 8 && opp_of(8) ==
 constexpr int QF = 0, QG = 9, QH = 14, NQ = 19;
 
 // ---- storage conversions -------------------------------------------------------
+// 32-bit mixing function (the MurmurHash3 finaliser): random bits for stochastic rounding.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x;
+}
+
+// st() rounds to nearest even; st_sr() rounds stochastically (up with probability
+// equal to the distance to the lower neighbour in ulps), so that the expected stored
+// value equals the computed one.  With 8-11 significand bits, rounding to nearest
+// makes per-step changes smaller than half an ulp vanish (the state stagnates);
+// stochastic rounding keeps them on average.
 template <typename S> struct Store;
 template <> struct Store<double> {
+    static constexpr bool kLow = false;
     __device__ static double ld(const double* p) { return *p; }
     __device__ static void st(double* p, double v) { *p = v; }
+    __device__ static void st_sr(double* p, double v, uint32_t) { *p = v; }
 };
 template <> struct Store<float> {
+    static constexpr bool kLow = false;
     __device__ static float ld(const float* p) { return *p; }
     __device__ static void st(float* p, float v) { *p = v; }
+    __device__ static void st_sr(float* p, float v, uint32_t) { *p = v; }
 };
 template <> struct Store<__nv_bfloat16> {
+    static constexpr bool kLow = true;
     __device__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     __device__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static void st_sr(__nv_bfloat16* p, float v, uint32_t r) {
+        // bfloat16 is the top half of the float: add 16 random bits below it, truncate
+        // (on the sign-magnitude encoding this rounds |v| away from zero with the right odds)
+        uint32_t b = __float_as_uint(v);
+        if ((b & 0x7F800000u) != 0x7F800000u) b += r & 0xFFFFu;
+        *p = __ushort_as_bfloat16((unsigned short)(b >> 16));
+    }
 };
 template <> struct Store<__half> {
+    static constexpr bool kLow = true;
     __device__ static float ld(const __half* p) { return __half2float(*p); }
     __device__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
+    __device__ static void st_sr(__half* p, float v, uint32_t r) {
+        const __half lo = __float2half_rz(v);                       // toward zero
+        const __half hi = __ushort_as_half((unsigned short)(__half_as_ushort(lo) + 1u));
+        const float flo = __half2float(lo);
+        const float d = fabsf(v) - fabsf(flo);                      // exact, in [0, ulp)
+        const float ulp = fabsf(__half2float(hi)) - fabsf(flo);
+        const float u01 = (float)(r >> 8) * (1.0f / 16777216.0f);
+        *p = (u01 * ulp < d) ? hi : lo;
+    }
 };
+
+// Store one of a node's populations: stochastic rounding for 16-bit storage when
+// enabled, with random bits drawn from the node's seed and the slot number k.
+template <typename S, typename R>
+__device__ __forceinline__ void put(S* p, R v, int sr, uint32_t seed, int k) {
+    if (Store<S>::kLow && sr)
+        Store<S>::st_sr(p, v, mix32(seed + (uint32_t)k * 0x9E3779B9u));
+    else
+        Store<S>::st(p, v);
+}
+
+// Per-node seed of the random stream: a hash of the node's index and of the bits of
+// two of its pre-collision populations.  The populations change from step to step,
+// so the stream does too, with no step counter (graph replay stays valid) and the
+// same result whenever the same state is stepped (runs are reproducible).
+template <typename R>
+__device__ __forceinline__ uint32_t node_seed(size_t node, R a, R b) {
+    const uint32_t ia = __float_as_uint((float)a), ib = __float_as_uint((float)b);
+    return mix32(ia ^ mix32(ib ^ mix32((uint32_t)node ^ (uint32_t)(node >> 32) * 0x27D4EB2Fu)));
+}
 
 // Compute type for a storage type: FP64 stays FP64, everything else is FP32.
 template <typename S> struct Real { using type = float; };
@@ -74,6 +131,7 @@ struct Coef {
     // w~ = varpi / 4, the anti-bounce-back constant in deviations.
     R wallT[4], wallC[4];
     int dirichlet_mask;        // bit s set: side s is Dirichlet for g and h, else adiabatic
+    int sr;                    // 1: stochastic rounding when storing 16-bit populations
 };
 
 template <typename R> __device__ __forceinline__ R sqrt_(R x);

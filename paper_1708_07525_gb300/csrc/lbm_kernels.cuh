@@ -117,13 +117,14 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
     const size_t self = (size_t)j * G.pitch + i;
     gather_pull<false, true>(src, G, i, j, c, f, g, h);
     load_hist(hist, G, self, hv);
+    const uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
     collide(c, f, g, h, hv);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) Store<S>::st(dst + (size_t)(QF + q) * G.plane + self, f[q]);
+    for (int q = 0; q < 9; ++q) put(dst + (size_t)(QF + q) * G.plane + self, f[q], c.sr, seed, q);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        Store<S>::st(dst + (size_t)(QG + q) * G.plane + self, g[q]);
-        Store<S>::st(dst + (size_t)(QH + q) * G.plane + self, h[q]);
+        put(dst + (size_t)(QG + q) * G.plane + self, g[q], c.sr, seed, QG + q);
+        put(dst + (size_t)(QH + q) * G.plane + self, h[q], c.sr, seed, QH + q);
     }
     store_hist(hist, G, self, hv);
 }
@@ -151,15 +152,16 @@ step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, G
     else
         gather_local<true>(buf, G, i, j, f, g, h);
     load_hist(hist, G, self, hv);
+    const uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
     collide(c, f, g, h, hv);
     if (!ODD) {
 #pragma unroll
         for (int q = 0; q < 9; ++q)
-            Store<S>::st(buf + (size_t)(QF + opp_of(q)) * G.plane + self, f[q]);
+            put(buf + (size_t)(QF + opp_of(q)) * G.plane + self, f[q], c.sr, seed, q);
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            Store<S>::st(buf + (size_t)(QG + opp_of(q)) * G.plane + self, g[q]);
-            Store<S>::st(buf + (size_t)(QH + opp_of(q)) * G.plane + self, h[q]);
+            put(buf + (size_t)(QG + opp_of(q)) * G.plane + self, g[q], c.sr, seed, QG + q);
+            put(buf + (size_t)(QH + opp_of(q)) * G.plane + self, h[q], c.sr, seed, QH + q);
         }
     } else {
 #pragma unroll
@@ -168,7 +170,7 @@ step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, G
             const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
             S* p = in ? buf + (size_t)(QF + q) * G.plane + (size_t)tj * G.pitch + ti
                       : buf + (size_t)(QF + opp_of(q)) * G.plane + self;
-            Store<S>::st(p, f[q]);
+            put(p, f[q], c.sr, seed, q);
         }
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
@@ -184,8 +186,8 @@ step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, G
                 vg = wall_value(c, c.wallT, push_side(q), vg);
                 vh = wall_value(c, c.wallC, push_side(q), vh);
             }
-            Store<S>::st(buf + (size_t)(QG + slot) * G.plane + off, vg);
-            Store<S>::st(buf + (size_t)(QH + slot) * G.plane + off, vh);
+            put(buf + (size_t)(QG + slot) * G.plane + off, vg, c.sr, seed, QG + q);
+            put(buf + (size_t)(QH + slot) * G.plane + off, vh, c.sr, seed, QH + q);
         }
     }
     store_hist(hist, G, self, hv);

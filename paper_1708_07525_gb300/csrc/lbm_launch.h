@@ -5,6 +5,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/lbm.h"
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -62,6 +63,11 @@ cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename 
                             int mode, double* snap, double* partial, double* out,
                             cudaStream_t st);
 int residual_blocks(const Geom& G);
+
+// Kernel constants of a cavity from its lattice parameters (lbm_api.cu);
+// stochastic rounding of 16-bit stores is enabled (Coef::sr = 1).
+template <typename R>
+Coef<R> make_coef(const lbm_params& P);
 
 // Read-only view of a context's device state, for entry points defined in
 // other translation units of the library.

@@ -48,6 +48,7 @@ class lbm_options(C.Structure):
         ("T_init", C.POINTER(C.c_double)), ("C_init", C.POINTER(C.c_double)),
         ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
         ("block_x", C.c_int), ("block_y", C.c_int), ("graph_chunk", C.c_int),
+        ("round_nearest", C.c_int),
     ]
 
 
@@ -161,7 +162,8 @@ class Cavity:
     def __init__(self, nx=None, ny=None, Ra=None, Da=None, eps=None, Pr=1.0, Le=1.0, N=1.0,
                  J=1.0, sigma=1.0, *, params: lbm_params | None = None, precision="f64",
                  layout="ab", Ma=0.0, varpi=0.0, seed=1, noise=1e-3, T_init=None, C_init=None,
-                 stream=None, allocator="torch", block=(0, 0), graph_chunk=0):
+                 stream=None, allocator="torch", block=(0, 0), graph_chunk=0,
+                 round_nearest=False):
         L = lib()
         o = lbm_options()
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -181,6 +183,7 @@ class Cavity:
             o.alloc, o.free = self._alloc.alloc, self._alloc.free
         o.block_x, o.block_y = int(block[0]), int(block[1])
         o.graph_chunk = int(graph_chunk)
+        o.round_nearest = int(bool(round_nearest))
         h = C.c_void_p()
         if params is not None:
             st = L.lbm_create_raw(C.byref(params), C.byref(o), C.byref(h))
@@ -268,3 +271,269 @@ class Cavity:
 
     def device_bytes(self) -> int:
         return int(lib().lbm_device_bytes(self.h))
+
+
+class lbm_instance(C.Structure):
+    _fields_ = [("params", lbm_params), ("seed", C.c_uint64), ("noise", C.c_double)]
+
+
+_batch_ready = False
+
+
+def _batch_lib():
+    global _batch_ready
+    L = lib()
+    if not _batch_ready:
+        P = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        L.lbm_batch_create.argtypes = [C.POINTER(lbm_instance), C.c_int, C.c_int, C.c_size_t,
+                                       C.POINTER(lbm_options), C.POINTER(C.c_void_p)]
+        L.lbm_batch_instance_bytes.argtypes = [lbm_grid, C.POINTER(lbm_options)]
+        L.lbm_batch_instance_bytes.restype = C.c_size_t
+        L.lbm_batch_add.argtypes = [P, C.POINTER(lbm_instance), C.POINTER(C.c_int)]
+        L.lbm_batch_remove.argtypes = [P, C.c_int]
+        L.lbm_batch_step.argtypes = [P, C.c_int64]
+        L.lbm_batch_time.argtypes = [P, C.c_int]
+        L.lbm_batch_time.restype = C.c_int64
+        L.lbm_batch_nusselt_sherwood.argtypes = [P, dp]
+        L.lbm_batch_residual.argtypes = [P, dp, C.POINTER(C.c_int)]
+        L.lbm_batch_fields.argtypes = [P, C.c_int, dp, dp, dp, dp, dp]
+        L.lbm_batch_autotune.argtypes = [P, C.c_int, C.c_char_p, C.c_size_t]
+        L.lbm_batch_set_tile.argtypes = [P, C.c_int, C.c_int, C.c_int]
+        L.lbm_batch_set_blocking.argtypes = [P, C.c_int, C.c_size_t]
+        L.lbm_batch_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+        L.lbm_batch_destroy.argtypes = [P]
+        L.lbm_batch_last_error.argtypes = [P]
+        L.lbm_batch_last_error.restype = C.c_char_p
+        for n in ("lbm_batch_create", "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step",
+                  "lbm_batch_nusselt_sherwood", "lbm_batch_residual", "lbm_batch_fields",
+                  "lbm_batch_autotune", "lbm_batch_info", "lbm_batch_set_tile",
+                  "lbm_batch_set_blocking"):
+            getattr(L, n).restype = C.c_int
+        _batch_ready = True
+    return L
+
+
+def _bcheck(status, handle=None):
+    if status != OK:
+        msg = _batch_lib().lbm_batch_last_error(handle).decode(errors="replace")
+        raise LbmError(status, msg)
+
+
+def make_instance(spec=None, *, params=None, seed=1, noise=1e-3) -> lbm_instance:
+    """Instance descriptor from a workloads.CavitySpec (or explicit lbm_params)."""
+    inst = lbm_instance()
+    if params is None:
+        params = lbm_derive_params(*spec.args(), varpi=getattr(spec, "varpi", 0.0))
+        seed, noise = spec.seed, spec.noise
+    inst.params = params
+    inst.seed = int(seed)
+    inst.noise = -1.0 if noise == 0 else float(noise)
+    return inst
+
+
+def _options(precision, layout, stream, allocator, graph_chunk, round_nearest):
+    o = lbm_options()
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+    if stream is not None:
+        o.stream = int(stream)
+    keep = None
+    if allocator == "torch":
+        keep = TorchAllocator()
+        o.alloc, o.free = keep.alloc, keep.free
+    o.graph_chunk = int(graph_chunk)
+    o.round_nearest = int(bool(round_nearest))
+    return o, keep
+
+
+def batch_instance_bytes(nx, ny, precision="f32", layout="ab") -> int:
+    o, _ = _options(precision, layout, None, None, 0, False)
+    return int(_batch_lib().lbm_batch_instance_bytes(lbm_grid(int(nx), int(ny)), C.byref(o)))
+
+
+class Batch:
+    """Many cavities advanced by one fused launch per step (wraps lbm_batch*)."""
+
+    def __init__(self, instances=(), capacity=None, arena_bytes=0, *, precision="f32", layout="ab",
+                 stream=None, allocator="torch", graph_chunk=0, round_nearest=False):
+        L = _batch_lib()
+        insts = list(instances)
+        cap = int(capacity if capacity is not None else max(1, len(insts)))
+        o, self._alloc = _options(precision, layout, stream, allocator, graph_chunk, round_nearest)
+        arr = (lbm_instance * max(1, len(insts)))(*insts) if insts else None
+        h = C.c_void_p()
+        _bcheck(L.lbm_batch_create(arr, len(insts), cap, int(arena_bytes), C.byref(o), C.byref(h)))
+        self.h = h
+        self.capacity = cap
+        self.shapes = {}
+        for k, inst in enumerate(insts):
+            self.shapes[k] = (inst.params.ny, inst.params.nx)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _batch_lib().lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def add(self, inst: lbm_instance) -> int:
+        slot = C.c_int(-1)
+        _bcheck(_batch_lib().lbm_batch_add(self.h, C.byref(inst), C.byref(slot)), self.h)
+        self.shapes[slot.value] = (inst.params.ny, inst.params.nx)
+        return slot.value
+
+    def remove(self, slot: int):
+        _bcheck(_batch_lib().lbm_batch_remove(self.h, int(slot)), self.h)
+        self.shapes.pop(slot, None)
+
+    def step(self, n=1):
+        _bcheck(_batch_lib().lbm_batch_step(self.h, int(n)), self.h)
+
+    def time(self, slot) -> int:
+        return int(_batch_lib().lbm_batch_time(self.h, int(slot)))
+
+    def nusselt_sherwood(self) -> np.ndarray:
+        out = np.zeros(4 * self.capacity)
+        _bcheck(_batch_lib().lbm_batch_nusselt_sherwood(self.h, _dptr(out)), self.h)
+        return out.reshape(self.capacity, 4)
+
+    def residual(self):
+        r = np.zeros(self.capacity)
+        d = (C.c_int * self.capacity)()
+        _bcheck(_batch_lib().lbm_batch_residual(self.h, _dptr(r), d), self.h)
+        return r, np.array(d[:], dtype=bool)
+
+    def fields(self, slot, which=("ux", "uy", "T", "C", "rho")):
+        shp = self.shapes[slot]
+        out = {k: np.empty(shp) for k in which}
+        args = [_dptr(out.get(k)) for k in ("ux", "uy", "T", "C", "rho")]
+        _bcheck(_batch_lib().lbm_batch_fields(self.h, int(slot), *args), self.h)
+        return out
+
+    def autotune(self, trial_steps=20) -> str:
+        buf = C.create_string_buffer(8192)
+        _bcheck(_batch_lib().lbm_batch_autotune(self.h, int(trial_steps), buf, 8192), self.h)
+        return buf.value.decode()
+
+    def set_tile(self, slot, tile_w, tile_h):
+        _bcheck(_batch_lib().lbm_batch_set_tile(self.h, int(slot), int(tile_w), int(tile_h)),
+                self.h)
+
+    def set_blocking(self, steps, l2_bytes=0):
+        _bcheck(_batch_lib().lbm_batch_set_blocking(self.h, int(steps), int(l2_bytes)), self.h)
+
+    def info(self):
+        cap, used = C.c_int(), C.c_int()
+        ab, au = C.c_size_t(), C.c_size_t()
+        _bcheck(_batch_lib().lbm_batch_info(self.h, C.byref(cap), C.byref(used), C.byref(ab),
+                                            C.byref(au)), self.h)
+        return {"capacity": cap.value, "used": used.value, "arena_bytes": ab.value,
+                "arena_used": au.value}
+
+
+class lbm_result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int), ("steps", C.c_int64),
+                ("residual", C.c_double), ("nush", C.c_double * 4), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+_server_ready = False
+
+
+def _server_lib():
+    global _server_ready
+    L = _batch_lib()
+    if not _server_ready:
+        P = C.c_void_p
+        L.lbm_server_create.argtypes = [C.c_size_t, C.c_int, C.c_int, C.POINTER(lbm_options),
+                                        C.POINTER(C.c_void_p)]
+        L.lbm_server_submit.argtypes = [P, C.POINTER(lbm_instance), C.c_double, C.c_double,
+                                        C.c_int64, C.c_int64]
+        L.lbm_server_tick.argtypes = [P, C.POINTER(C.c_int)]
+        L.lbm_server_poll.argtypes = [P, C.POINTER(lbm_result), C.c_int, C.POINTER(C.c_int)]
+        L.lbm_server_clock.argtypes = [P]
+        L.lbm_server_clock.restype = C.c_double
+        L.lbm_server_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
+        L.lbm_server_destroy.argtypes = [P]
+        L.lbm_server_last_error.argtypes = [P]
+        L.lbm_server_last_error.restype = C.c_char_p
+        for n in ("lbm_server_create", "lbm_server_submit", "lbm_server_tick", "lbm_server_poll",
+                  "lbm_server_info"):
+            getattr(L, n).restype = C.c_int
+        _server_ready = True
+    return L
+
+
+def _scheck(status, handle=None):
+    if status != OK:
+        msg = _server_lib().lbm_server_last_error(handle).decode(errors="replace")
+        raise LbmError(status, msg)
+
+
+class Server:
+    """Continuous-batching solver service (wraps lbm_server*)."""
+
+    def __init__(self, budget_bytes, max_slots=256, check_every=100, *, precision="bf16",
+                 layout="ab", stream=None, allocator="torch", graph_chunk=0, round_nearest=False):
+        L = _server_lib()
+        o, self._alloc = _options(precision, layout, stream, allocator, graph_chunk, round_nearest)
+        h = C.c_void_p()
+        _scheck(L.lbm_server_create(int(budget_bytes), int(max_slots), int(check_every),
+                                    C.byref(o), C.byref(h)))
+        self.h = h
+        self._buf = (lbm_result * 1024)()
+
+    def close(self):
+        if getattr(self, "h", None):
+            _server_lib().lbm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def submit(self, inst: lbm_instance, tol=1e-7, max_steps=10 ** 7, rid=0, nush_tol=0.0):
+        _scheck(_server_lib().lbm_server_submit(self.h, C.byref(inst), float(tol), float(nush_tol),
+                                                int(max_steps), int(rid)), self.h)
+
+    def tick(self) -> int:
+        n = C.c_int(0)
+        _scheck(_server_lib().lbm_server_tick(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def poll(self):
+        out = []
+        while True:
+            n = C.c_int(0)
+            _scheck(_server_lib().lbm_server_poll(self.h, self._buf, 1024, C.byref(n)), self.h)
+            for k in range(n.value):
+                r = self._buf[k]
+                out.append({"id": r.id, "status": r.status, "steps": r.steps,
+                            "residual": r.residual, "nush": list(r.nush), "t_submit": r.t_submit,
+                            "t_admit": r.t_admit, "t_done": r.t_done})
+            if n.value < 1024:
+                return out
+
+    def clock(self) -> float:
+        return float(_server_lib().lbm_server_clock(self.h))
+
+    def info(self):
+        q, a, d = C.c_int(), C.c_int(), C.c_int()
+        m = C.c_size_t()
+        _scheck(_server_lib().lbm_server_info(self.h, C.byref(q), C.byref(a), C.byref(d),
+                                              C.byref(m)), self.h)
+        return {"queued": q.value, "active": a.value, "done": d.value, "arena_used": m.value}
+
+    def drain(self, max_ticks=10 ** 7):
+        """Tick until queue and slots are empty; returns all results."""
+        res = []
+        for _ in range(max_ticks):
+            active = self.tick()
+            res += self.poll()
+            inf = self.info()
+            if active == 0 and inf["queued"] == 0:
+                break
+        return res + self.poll()

@@ -27,6 +27,7 @@ class CavitySpec:
     sigma: float = 1.0
     seed: int = 1
     noise: float = 1e-3
+    varpi: float = 0.4
 
     def args(self):
         return (self.nx, self.ny, self.Ra, self.Da, self.eps, self.Pr, self.Le, self.N, self.J,
@@ -54,26 +55,29 @@ PRECISION_STUDY = CavitySpec(1024, 1024, Ra=1e5, Da=1e-2, eps=0.6, Pr=1.0, Le=10
 NONPOROUS_A2 = CavitySpec(100, 200, Ra=1e5, Da=1e8, eps=1.0, Pr=1.0, Le=2.0, N=-0.8, seed=7)
 
 
+def stable_varpi(eps: float, sigma: float) -> float:
+    """The D2Q5 parameter varpi (Sec. 3.2, free in (0, 1); 2/5 in the paper's runs),
+    lowered where eps or sigma is small: the rest equilibria (sigma - varpi) T and
+    (eps - varpi) C of Eq. 28 must stay positive for a stable scheme."""
+    return min(0.4, 0.8 * min(eps, sigma))
+
+
 def draw_batch(count: int, seed: int, sizes=(32, 64, 128, 256)) -> list[CavitySpec]:
     """Mixed cavities: grid from `sizes` uniformly, log-uniform Ra in [1e3, 1e5] and
     Da in [1e-4, 1e-1], uniform eps in [0.3, 0.9], Le in [0.5, 10], N in [-5, 5],
-    sigma in [0.5, 2], Pr = J = 1."""
+    sigma in [0.5, 2], Pr = J = 1; varpi from stable_varpi()."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(count):
         n = int(rng.choice(sizes))
-        out.append(CavitySpec(
-            n, n,
-            Ra=float(10 ** rng.uniform(3, 5)),
-            Da=float(10 ** rng.uniform(-4, -1)),
-            eps=float(rng.uniform(0.3, 0.9)),
-            Pr=1.0,
-            Le=float(rng.uniform(0.5, 10)),
-            N=float(rng.uniform(-5, 5)),
-            J=1.0,
-            sigma=float(rng.uniform(0.5, 2.0)),
-            seed=int(rng.integers(1, 2 ** 31)),
-        ))
+        Ra = float(10 ** rng.uniform(3, 5))
+        Da = float(10 ** rng.uniform(-4, -1))
+        eps = float(rng.uniform(0.3, 0.9))
+        Le = float(rng.uniform(0.5, 10))
+        N = float(rng.uniform(-5, 5))
+        sigma = float(rng.uniform(0.5, 2.0))
+        out.append(CavitySpec(n, n, Ra=Ra, Da=Da, eps=eps, Pr=1.0, Le=Le, N=N, J=1.0, sigma=sigma,
+                              seed=int(rng.integers(1, 2 ** 31)), varpi=stable_varpi(eps, sigma)))
     return out
 
 
