@@ -246,7 +246,7 @@ lbm_status lbm_batch_fields(lbm_batch* b, int slot, double* ux, double* uy, doub
                             double* rho);
 
 /* Choose the tile shape of every grid size present in the batch by timing
- * candidate shapes (widths 32-256, heights 1-16) over `trial_steps` steps on
+ * candidate shapes (128-node tiles 32, 64 or 128 wide) over `trial_steps` steps on
  * scratch cavities of that size (the batch's own state is not touched), and
  * apply them.  The choice is cached per (nx, ny, precision, layout) for the
  * process and used by later batches.  report (may be NULL, `cap` chars)

@@ -119,13 +119,14 @@ struct Slot {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;   // (nx,ny,prec,layout) -> (log2 w, h)
 
+// Default tile: BATCH_THREADS nodes (one per thread), as wide as the cavity allows.
 void default_tile(int nx, int* wlog2, int* th) {
     int w = 32;
-    while (w < nx && w < 128) w <<= 1;
+    while (w < nx && w < BATCH_THREADS) w <<= 1;
     int l = 0;
     while ((1 << l) < w) ++l;
     *wlog2 = l;
-    *th = std::max(1, 512 / w);
+    *th = std::max(1, BATCH_THREADS / w);
 }
 
 }  // namespace
@@ -174,6 +175,7 @@ struct lbm_batch {
     std::vector<BatchInst<float>> h_table;
     std::vector<int> h_owner, h_ntiles;
     int total_tiles = 0;
+    bool one_node_tiles = false;         // every tile has BATCH_THREADS nodes
     // L2 temporal blocking: groups of cavities whose working set fits in a share of
     // L2 are advanced `tblock` steps each before the next group is touched.
     std::vector<std::pair<int, int>> groups;   // [tile_begin, tile_end)
@@ -306,6 +308,10 @@ lbm_status sync_tables(lbm_batch* b) {
         W.L = s.P.nx;
     }
     b->total_tiles = tiles;
+    b->one_node_tiles = true;
+    for (int k = 0; k < b->capacity; ++k)
+        if (b->slots[k].used && (1 << b->slots[k].tw_log2) * b->slots[k].th != BATCH_THREADS)
+            b->one_node_tiles = false;
     // groups: consecutive cavities while their per-step working set (buffers read
     // and written, history) stays within the L2 budget
     b->groups.clear();
@@ -367,10 +373,11 @@ int reduce_grid(const lbm_batch* b) {
 
 cudaError_t launch_range(lbm_batch* b, int tile_begin, int tile_end, int parity) {
     const bool aa = b->layout == LBM_AA;
+    const bool one = b->one_node_tiles;
     switch (b->prec) {
-        case LBM_F32: return launch_batch_step<float>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, b->stream);
-        case LBM_BF16: return launch_batch_step<__nv_bfloat16>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, b->stream);
-        default: return launch_batch_step<__half>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, b->stream);
+        case LBM_F32: return launch_batch_step<float>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, b->stream);
+        case LBM_BF16: return launch_batch_step<__nv_bfloat16>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, b->stream);
+        default: return launch_batch_step<__half>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, b->stream);
     }
 }
 
@@ -477,7 +484,7 @@ lbm_status lbm_batch_create(const lbm_instance* inst, int count, int capacity, s
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     int l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device);
-    if (l2 > 0) b->l2_budget = (size_t)l2 / 2;
+    if (l2 > 0) b->l2_budget = (size_t)l2 * 3 / 4;
     if (O.stream) {
         b->stream = (cudaStream_t)O.stream;
     } else {
@@ -799,12 +806,13 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, char* report, size_
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        for (int wl = 5; wl <= 8; ++wl) {
+        // candidates: tiles of one node per thread (the loop-free kernel), 32..128 wide
+        for (int wl = 5; wl <= 7; ++wl) {
             const int w = 1 << wl;
             if (w > 2 * std::max(32, nx)) continue;       // more than half a tile would be idle
             for (int h = 1; h <= 16; h <<= 1) {
                 const int nodes = w * h;
-                if (nodes < 128 || nodes > 2048) continue;
+                if (nodes != BATCH_THREADS) continue;
                 for (int q = 0; q < count; ++q) {
                     s->slots[q].tw_log2 = wl;
                     s->slots[q].th = h;
@@ -845,6 +853,14 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, char* report, size_
         rep += line;
     }
     invalidate(b);
+    {
+        lbm_status s2 = sync_tables(b);
+        if (s2 != LBM_OK) return s2;
+        char line[128];
+        std::snprintf(line, sizeof line, "# groups %zu l2_budget %zu tiles %d\n", b->groups.size(),
+                      b->l2_budget, b->total_tiles);
+        rep += line;
+    }
     if (report && cap) {
         std::strncpy(report, rep.c_str(), cap - 1);
         report[cap - 1] = 0;

@@ -39,10 +39,9 @@ __device__ __forceinline__ void load_inst(const BatchInst<R>* __restrict__ table
 }
 
 // One time step of every active cavity.  tile_owner[t] = cavity of global tile t.
-// Launched with one CTA per tile (the loop then runs once); the register cap keeps
-// five CTAs resident per SM so that enough loads are in flight.
+// Launched with one CTA per tile (the loop then runs once).
 template <typename S, bool AA>
-__global__ void __launch_bounds__(BATCH_THREADS, 5)
+__global__ void __launch_bounds__(BATCH_THREADS, 4)
 batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
                   const int* __restrict__ tile_owner, int tile_begin, int tile_end, int parity) {
     using R = typename Real<S>::type;
@@ -70,7 +69,7 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
                 S* dst = (S*)I.buf[odd ^ 1];
                 gather_pull<false, true>(src, G, i, j, I.c, f, g, h);
                 load_hist(hist, G, self, hv);
-                const uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
+                uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
                 collide(I.c, f, g, h, hv);
 #pragma unroll
                 for (int q = 0; q < 9; ++q)
@@ -87,7 +86,7 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
                 else
                     gather_local<true>(buf, G, i, j, f, g, h);
                 load_hist(hist, G, self, hv);
-                const uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
+                uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
                 collide(I.c, f, g, h, hv);
                 if (!odd) {
 #pragma unroll
@@ -131,6 +130,94 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
             store_hist(hist, G, self, hv);
         }
     }
+}
+
+// The same step for tiles of exactly BATCH_THREADS nodes: one node per thread,
+// one tile per CTA and no loop, so nothing loop-invariant is hoisted into
+// registers (the descriptor stays in shared memory and occupancy stays high).
+template <typename S, bool AA>
+__global__ void __launch_bounds__(BATCH_THREADS)
+batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
+                   const int* __restrict__ tile_owner, int tile_begin, int parity) {
+    using R = typename Real<S>::type;
+    __shared__ BatchInst<R> I;
+    const int tile = tile_begin + blockIdx.x;
+    load_inst(table, tile_owner[tile], I);
+    __syncthreads();
+    if (!I.active) return;
+    const int local = tile - I.tile_begin;
+    const int ty = local / I.tiles_x, tx = local - ty * I.tiles_x;
+    const int n = threadIdx.x;
+    const int i = (tx << I.tile_w_log2) + (n & ((1 << I.tile_w_log2) - 1));
+    const int j = ty * I.tile_h + (n >> I.tile_w_log2);
+    const Geom G = I.G;
+    if (i >= G.nx || j >= G.ny) return;
+    const int odd = (parity + I.phase) & 1;
+    R f[9], g[5], h[5], hv[4];
+    const size_t self = (size_t)j * G.pitch + i;
+    R* hist = (R*)I.hist;
+    if (!AA) {
+        const S* src = (const S*)I.buf[odd];
+        S* dst = (S*)I.buf[odd ^ 1];
+        gather_pull<false, true>(src, G, i, j, I.c, f, g, h);
+        load_hist(hist, G, self, hv);
+        uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
+        collide(I.c, f, g, h, hv);
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            put(dst + (size_t)(QF + q) * G.plane + self, f[q], I.c.sr, seed, q);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            put(dst + (size_t)(QG + q) * G.plane + self, g[q], I.c.sr, seed, QG + q);
+            put(dst + (size_t)(QH + q) * G.plane + self, h[q], I.c.sr, seed, QH + q);
+        }
+    } else {
+        S* buf = (S*)I.buf[0];
+        if (odd)
+            gather_pull<true, true>(buf, G, i, j, I.c, f, g, h);
+        else
+            gather_local<true>(buf, G, i, j, f, g, h);
+        load_hist(hist, G, self, hv);
+        uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
+        collide(I.c, f, g, h, hv);
+        if (!odd) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                put(buf + (size_t)(QF + opp_of(q)) * G.plane + self, f[q], I.c.sr, seed, q);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                put(buf + (size_t)(QG + opp_of(q)) * G.plane + self, g[q], I.c.sr, seed, QG + q);
+                put(buf + (size_t)(QH + opp_of(q)) * G.plane + self, h[q], I.c.sr, seed, QH + q);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const int ti = i + ex_of(q), tj = j + ey_of(q);
+                const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
+                S* p = in ? buf + (size_t)(QF + q) * G.plane + (size_t)tj * G.pitch + ti
+                          : buf + (size_t)(QF + opp_of(q)) * G.plane + self;
+                put(p, f[q], I.c.sr, seed, q);
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const int ti = i + ex_of(q), tj = j + ey_of(q);
+                const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
+                R vg = g[q], vh = h[q];
+                size_t off = self;
+                int slot = opp_of(q);
+                if (in) {
+                    off = (size_t)tj * G.pitch + ti;
+                    slot = q;
+                } else if (q > 0) {
+                    vg = wall_value(I.c, I.c.wallT, push_side(q), vg);
+                    vh = wall_value(I.c, I.c.wallC, push_side(q), vh);
+                }
+                put(buf + (size_t)(QG + slot) * G.plane + off, vg, I.c.sr, seed, QG + q);
+                put(buf + (size_t)(QH + slot) * G.plane + off, vh, I.c.sr, seed, QH + q);
+            }
+        }
+    }
+    store_hist(hist, G, self, hv);
 }
 
 // Gather mode of cavity I at batch step parity `parity`.

@@ -68,9 +68,10 @@ template <> struct Store<__nv_bfloat16> {
     __device__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
     __device__ static void st_sr(__nv_bfloat16* p, float v, uint32_t r) {
         // bfloat16 is the top half of the float: add 16 random bits below it, truncate
-        // (on the sign-magnitude encoding this rounds |v| away from zero with the right odds)
+        // (on the sign-magnitude encoding this rounds |v| away from zero with the right
+        // odds).  Non-finite values pass unchanged (their low bits are not touched).
         uint32_t b = __float_as_uint(v);
-        if ((b & 0x7F800000u) != 0x7F800000u) b += r & 0xFFFFu;
+        b += ((b & 0x7F800000u) != 0x7F800000u) ? (r & 0xFFFFu) : 0u;
         *p = __ushort_as_bfloat16((unsigned short)(b >> 16));
     }
 };
@@ -84,19 +85,23 @@ template <> struct Store<__half> {
         const float flo = __half2float(lo);
         const float d = fabsf(v) - fabsf(flo);                      // exact, in [0, ulp)
         const float ulp = fabsf(__half2float(hi)) - fabsf(flo);
-        const float u01 = (float)(r >> 8) * (1.0f / 16777216.0f);
+        const float u01 = (float)(r >> 16) * (1.0f / 65536.0f);
         *p = (u01 * ulp < d) ? hi : lo;
     }
 };
 
 // Store one of a node's populations: stochastic rounding for 16-bit storage when
-// enabled, with random bits drawn from the node's seed and the slot number k.
+// enabled.  The random bits come from a per-node linear congruential stream
+// (Knuth's MMIX constants) seeded by node_seed(); only its high 16 bits are used,
+// which is enough for rounding decisions and costs one multiply-add per value.
 template <typename S, typename R>
-__device__ __forceinline__ void put(S* p, R v, int sr, uint32_t seed, int k) {
-    if (Store<S>::kLow && sr)
-        Store<S>::st_sr(p, v, mix32(seed + (uint32_t)k * 0x9E3779B9u));
-    else
+__device__ __forceinline__ void put(S* p, R v, int sr, uint32_t& state, int) {
+    if (Store<S>::kLow && sr) {
+        state = state * 1664525u + 1013904223u;
+        Store<S>::st_sr(p, v, (state >> 16) | (state & 0xFFFF0000u));
+    } else {
         Store<S>::st(p, v);
+    }
 }
 
 // Per-node seed of the random stream: a hash of the node's index and of the bits of

@@ -117,7 +117,7 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
     const size_t self = (size_t)j * G.pitch + i;
     gather_pull<false, true>(src, G, i, j, c, f, g, h);
     load_hist(hist, G, self, hv);
-    const uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
+    uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
     collide(c, f, g, h, hv);
 #pragma unroll
     for (int q = 0; q < 9; ++q) put(dst + (size_t)(QF + q) * G.plane + self, f[q], c.sr, seed, q);
@@ -152,7 +152,7 @@ step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, G
     else
         gather_local<true>(buf, G, i, j, f, g, h);
     load_hist(hist, G, self, hv);
-    const uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
+    uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
     collide(c, f, g, h, hv);
     if (!ODD) {
 #pragma unroll

@@ -109,7 +109,7 @@ def test_autotune_keeps_results_and_residual_per_slot():
     a = lbm.Batch(insts, precision="f32")
     c = lbm.Batch(insts, precision="f32")
     rep = a.autotune(trial_steps=6)
-    lines = [ln.split() for ln in rep.strip().splitlines()]
+    lines = [ln.split() for ln in rep.strip().splitlines() if not ln.startswith("#")]
     assert {(int(x[0]), int(x[1])) for x in lines} == {(i.params.nx, i.params.ny) for i in insts}
     for x in lines:
         assert int(x[2]) in (32, 64, 128, 256) and float(x[4]) > 0
