@@ -125,6 +125,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (the timing rule: the job is as slow as its
+    slowest rank); x itself on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput: units processed by all ranks / the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def dist_setup(n_gpus):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -246,12 +263,9 @@ def run_ours(args):
     barrier()
     total_ms = start.elapsed_time(stop)
     kernel_ms = sum(a.elapsed_time(b) for a, b in evs) / (args.steps * k)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, device="cuda")
     nodes = n * n
-    value = world * nodes * k * args.steps / (total_ms / 1e3) / 1e9
+    value = aggregate_value(nodes * k * args.steps, total_ms / 1e3, world) / 1e9
 
     # end to end through the public API with host buffers: each step re-initialises the
     # cavity from pinned host T/C fields (H2D), runs the 100 time steps, and reads the
@@ -274,12 +288,8 @@ def run_ours(args):
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * nodes * k * args.steps / e2e_s / 1e9
+    e2e_s = max_over_ranks(time.perf_counter() - t0, device="cuda")
+    e2e_value = aggregate_value(nodes * k * args.steps, e2e_s, world) / 1e9
 
     peak, peak_kind = measured_peaks()
     bpn = BYTES_PER_NODE[args.precision]
@@ -439,8 +449,14 @@ def run_serve(args):
 
     # plain path: one FP64 cavity at a time, same check interval, residual < fp64_tol
     plain = {}
+    plain_s = None
+    if args.plain_cache and os.path.exists(args.plain_cache):
+        with open(args.plain_cache) as f:
+            cached = json.load(f)
+        plain = {int(k): v for k, v in cached["plain"].items()}
+        plain_s = cached["seconds"]
     t0 = time.perf_counter()
-    for k, s in enumerate(specs):
+    for k, s in enumerate(specs if plain_s is None else []):
         if time.perf_counter() - t0 > args.plain_budget_s:
             break
         c = lbm.Cavity(*s.args(), varpi=s.varpi, precision="f64", seed=s.seed, noise=s.noise,
@@ -455,7 +471,11 @@ def run_serve(args):
                 break
         plain[k] = {"nush": c.nusselt_sherwood().tolist(), "steps": steps, "status": status}
         c.close()
-    plain_s = time.perf_counter() - t0
+    if plain_s is None:
+        plain_s = time.perf_counter() - t0
+        if args.plain_cache:
+            with open(args.plain_cache, "w") as f:
+                json.dump({"plain": plain, "seconds": plain_s}, f)
     errs = []
     for k, p in plain.items():
         if p["status"] == "ok" and served[k]["status"] == 0:
@@ -488,6 +508,56 @@ def run_serve(args):
     return 0
 
 
+def run_precision(args):
+    """Storage-precision study on the 1024^2 cavity (Ra 1e5, Da 1e-2, eps 0.6, Le 10,
+    N 2): FP64 (reference), FP32, and shifted FP16 / BF16 with stochastic rounding,
+    all FP32 arithmetic but FP64; the same number of steps; errors of u, T, C
+    (relative L2) and of Nu/Sh against FP64; FP64 reductions throughout."""
+    import numpy as np
+    import torch
+    from paper_1708_07525_gb300 import lbm
+    from paper_1708_07525_gb300.workloads import PRECISION_STUDY as spec
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    steps, check = args.prec_steps, args.prec_check
+    out = {}
+    ref = None
+    for prec in args.prec_list.split(","):
+        c = lbm.Cavity(*spec.args(), precision=prec, seed=spec.seed, noise=spec.noise,
+                       stream=stream.cuda_stream)
+        c.residual()
+        hist = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        while c.t < steps:
+            e0.record(stream)
+            c.step(min(check, steps - c.t))
+            e1.record(stream)
+            r = c.residual()
+            ms += e0.elapsed_time(e1)
+            hist.append([c.t, r] + c.nusselt_sherwood().tolist())
+        fl = c.fields(("ux", "uy", "T", "C"))
+        rec = {"glups": spec.nx * spec.ny * steps / (ms / 1e3) / 1e9, "final_residual": hist[-1][1],
+               "nush": hist[-1][2:], "history": hist}
+        if ref is None:
+            ref = (fl, np.array(hist[-1][2:]))
+        else:
+            rec["rel_l2_err"] = {k: float(np.linalg.norm(fl[k] - ref[0][k]) / np.linalg.norm(ref[0][k]))
+                                 for k in fl}
+            rec["nush_rel_err"] = float(np.max(np.abs(np.array(hist[-1][2:]) - ref[1]) / np.abs(ref[1])))
+        out[prec] = rec
+        c.close()
+        with open(os.path.join(ROOT, "gpurun_out", "precision_partial.json"), "w") as f:
+            json.dump(out, f)
+    line = {"metric": METRIC, "mode": "precision", "unit": "relative error", "data": "synthetic",
+            "config": {"workload": f"{spec.nx}x{spec.ny} cavity Ra={spec.Ra} Da={spec.Da} eps={spec.eps} "
+                                   f"Le={spec.Le} N={spec.N}", "steps": steps, "check_every": check},
+            "results": {k: {kk: vv for kk, vv in v.items() if kk != "history"} for k, v in out.items()}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,7 +572,10 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"])
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "precision"])
+    ap.add_argument("--prec-steps", type=int, default=2500000)
+    ap.add_argument("--prec-check", type=int, default=100000)
+    ap.add_argument("--prec-list", default="f64,f32,f16,bf16")
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--requests", type=int, default=32)
@@ -514,11 +587,15 @@ def main():
     ap.add_argument("--max-steps", type=int, default=300000)
     ap.add_argument("--budget-gb", type=float, default=8.0)
     ap.add_argument("--plain-budget-s", type=float, default=120.0)
+    ap.add_argument("--plain-cache", default="")
     args = ap.parse_args()
     if args.mode == "batch":
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "precision":
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        return run_precision(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -165,6 +165,12 @@ int64_t lbm_time(const lbm_ctx* ctx);
 lbm_status lbm_fields(lbm_ctx* ctx, double* ux, double* uy, double* T, double* C,
                       double* rho);
 
+/* The same fields over the window of nodes [x0, x0 + w) x [y0, y0 + h) only, into
+ * caller-owned host arrays [h][w] (for grids too large to copy whole).
+ * LBM_ERR_INVALID if the window leaves the grid or h > 65535. */
+lbm_status lbm_fields_window(lbm_ctx* ctx, int x0, int y0, int w, int h, double* ux, double* uy,
+                             double* T, double* C, double* rho);
+
 /* Mean Nusselt and Sherwood numbers on the left and right walls (Eq. 38),
  * out = {Nu_L, Sh_L, Nu_R, Sh_R}, reduced in FP64.  The wall gradient is the
  * second-order one-sided difference through the wall value and the two

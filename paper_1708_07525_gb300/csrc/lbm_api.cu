@@ -2,6 +2,7 @@
 // mapping, stepping with CUDA-graph replay, read-outs, checkpoints.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -114,7 +115,8 @@ struct lbm_ctx {
     void* buf[2] = {nullptr, nullptr};
     void* hist = nullptr;
     double* d_out = nullptr;        // 16 doubles: Nu/Sh and residual results
-    double* d_fields = nullptr;     // lazily allocated [5][ny][nx]
+    double* d_fields = nullptr;     // lazily allocated [5][h][w] read-out window
+    size_t fields_cap = 0;          // nodes d_fields holds
     double* d_snap = nullptr;       // lazily allocated [4][ny][nx]
     double* d_partial = nullptr;    // lazily allocated residual partials
     double* d_stage = nullptr;      // lazily allocated [2][ny][nx] initial-field staging
@@ -425,6 +427,13 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
     int bx = O.block_x, by = O.block_y;
     if (bx == 0) bx = nx >= 128 ? 128 : 32;
     if (by == 0) by = bx >= 128 ? 1 : 128 / bx;
+    if ((ny + by - 1) / by > 65535) {   // the launch grid's y extent
+        lbm_status s = c->fail(LBM_ERR_INVALID, "lbm_create: ny = %d needs block_y >= %d", ny,
+                               (ny + 65534) / 65535);
+        g_last_error = c->err;
+        lbm_destroy(c);
+        return s;
+    }
     c->L.bx = bx;
     c->L.by = by;
     c->L.stream = c->stream;
@@ -535,23 +544,30 @@ lbm_status lbm_step(lbm_ctx* c, int64_t n) {
 
 int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 
-lbm_status lbm_fields(lbm_ctx* c, double* ux, double* uy, double* T, double* C, double* rho) {
+lbm_status lbm_fields_window(lbm_ctx* c, int x0, int y0, int w, int h, double* ux, double* uy,
+                             double* T, double* C, double* rho) {
     if (!c) {
-        set_global_error("lbm_fields: NULL context");
+        set_global_error("lbm_fields_window: NULL context");
         return LBM_ERR_INVALID;
     }
+    if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || x0 + w > c->G.nx || y0 + h > c->G.ny || h > 65535)
+        return c->fail(LBM_ERR_INVALID, "lbm_fields_window: window (%d, %d, %d x %d) outside the %d x %d grid",
+                       x0, y0, w, h, c->G.nx, c->G.ny);
     DeviceGuard dg(c->device);
-    const size_t n = c->nodes();
-    if (!c->d_fields) {
+    const size_t n = (size_t)w * h;
+    if (n > c->fields_cap) {
+        c->dfree(c->d_fields, 5 * c->fields_cap * sizeof(double));
+        c->fields_cap = 0;
         c->d_fields = (double*)c->dalloc(5 * n * sizeof(double));
         if (!c->d_fields) return c->fail(LBM_ERR_NOMEM, "lbm_fields: no device memory for read-out");
+        c->fields_cap = n;
     }
     const int mode = c->read_mode();
     const void* b = cur_buf(c);
-    cudaError_t e = LBM_DISPATCH(c, launch_fields<double>(b, c->G, c->cd, mode, c->d_fields, c->stream),
-                                 launch_fields<float>(b, c->G, c->cf, mode, c->d_fields, c->stream),
-                                 launch_fields<__nv_bfloat16>(b, c->G, c->cf, mode, c->d_fields, c->stream),
-                                 launch_fields<__half>(b, c->G, c->cf, mode, c->d_fields, c->stream));
+    cudaError_t e = LBM_DISPATCH(c, launch_fields<double>(b, c->G, c->cd, mode, x0, y0, w, h, c->d_fields, c->stream),
+                                 launch_fields<float>(b, c->G, c->cf, mode, x0, y0, w, h, c->d_fields, c->stream),
+                                 launch_fields<__nv_bfloat16>(b, c->G, c->cf, mode, x0, y0, w, h, c->d_fields, c->stream),
+                                 launch_fields<__half>(b, c->G, c->cf, mode, x0, y0, w, h, c->d_fields, c->stream));
     double* outs[5] = {ux, uy, T, C, rho};
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)
         if (outs[k])
@@ -559,6 +575,24 @@ lbm_status lbm_fields(lbm_ctx* c, double* ux, double* uy, double* T, double* C, 
                                 cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return c->cuda_fail(e, "lbm_fields");
+    return LBM_OK;
+}
+
+lbm_status lbm_fields(lbm_ctx* c, double* ux, double* uy, double* T, double* C, double* rho) {
+    if (!c) {
+        set_global_error("lbm_fields: NULL context");
+        return LBM_ERR_INVALID;
+    }
+    // whole grid, in row bands of at most 65535 rows and about 2^26 nodes (2.7 GB of read-out)
+    const int band = (int)std::max<size_t>(1, std::min<size_t>(65535, ((size_t)1 << 26) / c->G.nx));
+    if (c->G.ny <= band) return lbm_fields_window(c, 0, 0, c->G.nx, c->G.ny, ux, uy, T, C, rho);
+    for (int y0 = 0; y0 < c->G.ny; y0 += band) {
+        const int h = std::min(band, c->G.ny - y0);
+        const size_t off = (size_t)y0 * c->G.nx;
+        lbm_status s = lbm_fields_window(c, 0, y0, c->G.nx, h, ux ? ux + off : nullptr, uy ? uy + off : nullptr,
+                                         T ? T + off : nullptr, C ? C + off : nullptr, rho ? rho + off : nullptr);
+        if (s != LBM_OK) return s;
+    }
     return LBM_OK;
 }
 
@@ -733,7 +767,7 @@ void lbm_destroy(lbm_ctx* c) {
     c->dfree(c->buf[1], c->state_bytes());
     c->dfree(c->hist, c->hist_bytes());
     c->dfree(c->d_out, 64 * sizeof(double));
-    c->dfree(c->d_fields, 5 * c->nodes() * sizeof(double));
+    c->dfree(c->d_fields, 5 * c->fields_cap * sizeof(double));
     c->dfree(c->d_snap, 4 * c->nodes() * sizeof(double));
     c->dfree(c->d_partial, (size_t)residual_blocks(c->G) * 9 * sizeof(double));
     c->dfree(c->d_stage, 2 * c->nodes() * sizeof(double));

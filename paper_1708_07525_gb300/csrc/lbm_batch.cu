@@ -751,9 +751,9 @@ lbm_status lbm_batch_fields(lbm_batch* b, int slot, double* ux, double* uy, doub
     const void* cur = b->cur_of(s);
     cudaError_t e;
     switch (b->prec) {
-        case LBM_F32: e = launch_fields<float>(cur, s.G, c, mode, b->d_fields, b->stream); break;
-        case LBM_BF16: e = launch_fields<__nv_bfloat16>(cur, s.G, c, mode, b->d_fields, b->stream); break;
-        default: e = launch_fields<__half>(cur, s.G, c, mode, b->d_fields, b->stream); break;
+        case LBM_F32: e = launch_fields<float>(cur, s.G, c, mode, 0, 0, s.G.nx, s.G.ny, b->d_fields, b->stream); break;
+        case LBM_BF16: e = launch_fields<__nv_bfloat16>(cur, s.G, c, mode, 0, 0, s.G.nx, s.G.ny, b->d_fields, b->stream); break;
+        default: e = launch_fields<__half>(cur, s.G, c, mode, 0, 0, s.G.nx, s.G.ny, b->d_fields, b->stream); break;
     }
     double* outs[5] = {ux, uy, T, C, rho};
     for (int k = 0; k < 5 && e == cudaSuccess; ++k)

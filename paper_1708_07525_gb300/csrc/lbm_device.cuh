@@ -75,18 +75,20 @@ template <> struct Store<__nv_bfloat16> {
         *p = __ushort_as_bfloat16((unsigned short)(b >> 16));
     }
 };
+// FP16 holds the deviations scaled by 2^12 (exact in both directions), so that
+// deviations down to ~1.5e-8 sit in FP16's normal range (11 significant bits)
+// instead of its subnormals; |deviation| must stay below 16 (65504 / 2^12).
 template <> struct Store<__half> {
     static constexpr bool kLow = true;
-    __device__ static float ld(const __half* p) { return __half2float(*p); }
-    __device__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
+    static constexpr float kScale = 4096.0f, kInvScale = 1.0f / 4096.0f;
+    __device__ static float ld(const __half* p) { return __half2float(*p) * kInvScale; }
+    __device__ static void st(__half* p, float v) { *p = __float2half_rn(v * kScale); }
     __device__ static void st_sr(__half* p, float v, uint32_t r) {
-        const __half lo = __float2half_rz(v);                       // toward zero
-        const __half hi = __ushort_as_half((unsigned short)(__half_as_ushort(lo) + 1u));
-        const float flo = __half2float(lo);
-        const float d = fabsf(v) - fabsf(flo);                      // exact, in [0, ulp)
-        const float ulp = fabsf(__half2float(hi)) - fabsf(flo);
-        const float u01 = (float)(r >> 16) * (1.0f / 65536.0f);
-        *p = (u01 * ulp < d) ? hi : lo;
+        // In FP16's normal range the 13 float mantissa bits below the 10 kept ones are
+        // the fraction of an FP16 ulp: add 13 random bits there, then truncate.
+        uint32_t b = __float_as_uint(v * kScale);
+        b += ((b & 0x7F800000u) != 0x7F800000u) ? (r & 0x1FFFu) : 0u;
+        *p = __float2half_rz(__uint_as_float(b));
     }
 };
 

@@ -277,18 +277,20 @@ __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restr
 }
 
 // ---- read-outs -----------------------------------------------------------------------
-// Fields at the current level: out planes [5][ny][nx] = ux, uy, T, C, rho (FP64).
+// Fields at the current level over the window [x0, x0 + w) x [y0, y0 + h):
+// out planes [5][h][w] = ux, uy, T, C, rho (FP64).
 template <typename S>
 __global__ void fields_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c,
-                              int mode, double* __restrict__ out) {
+                              int mode, int x0, int y0, int w, int h, double* __restrict__ out) {
     using R = typename Real<S>::type;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
-    R f[9], g[5], h[5];
-    gather<true>(mode, buf, G, i, j, c, f, g, h);
-    Macro<R> M = macro(c, f, g, h);
-    const size_t n = (size_t)G.nx * G.ny, k = (size_t)j * G.nx + i;
+    const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+    const int wj = blockIdx.y * blockDim.y + threadIdx.y;
+    if (wi >= w || wj >= h) return;
+    const int i = x0 + wi, j = y0 + wj;
+    R f[9], g[5], hh[5];
+    gather<true>(mode, buf, G, i, j, c, f, g, hh);
+    Macro<R> M = macro(c, f, g, hh);
+    const size_t n = (size_t)w * h, k = (size_t)wj * w + wi;
     out[k] = (double)M.ux;
     out[n + k] = (double)M.uy;
     out[2 * n + k] = (double)c.T0 + (double)M.Tp;

@@ -51,9 +51,10 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
 template <typename S>
 cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
                            const Coef<typename Real<S>::type>& c, bool odd, const LaunchCfg& L);
+// Fields over the window [x0, x0 + w) x [y0, y0 + h) into out[5][h][w].
 template <typename S>
 cudaError_t launch_fields(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
-                          int mode, double* out, cudaStream_t st);
+                          int mode, int x0, int y0, int w, int h, double* out, cudaStream_t st);
 template <typename S>
 cudaError_t launch_nush(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
                         int mode, const WallSpec& W, double* out, cudaStream_t st);

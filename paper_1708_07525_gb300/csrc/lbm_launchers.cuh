@@ -44,9 +44,10 @@ cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
 
 template <typename S>
 cudaError_t launch_fields(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
-                          int mode, double* out, cudaStream_t st) {
-    dim3 b(128, 1), gr = grid_for(G, 128, 1);
-    fields_kernel<S><<<gr, b, 0, st>>>((const S*)buf, G, c, mode, out);
+                          int mode, int x0, int y0, int w, int h, double* out, cudaStream_t st) {
+    if (w <= 0 || h <= 0) return cudaSuccess;
+    dim3 b(128, 1), gr((unsigned)((w + 127) / 128), (unsigned)h, 1);
+    fields_kernel<S><<<gr, b, 0, st>>>((const S*)buf, G, c, mode, x0, y0, w, h, out);
     return cudaGetLastError();
 }
 
@@ -79,8 +80,8 @@ cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename 
                                            const Coef<Real<S>::type>&, bool,                   \
                                            const LaunchCfg&);                                  \
     template cudaError_t launch_fields<S>(const void*, const Geom&,                            \
-                                          const Coef<Real<S>::type>&, int, double*,            \
-                                          cudaStream_t);                                       \
+                                          const Coef<Real<S>::type>&, int, int, int, int, int, \
+                                          double*, cudaStream_t);                              \
     template cudaError_t launch_nush<S>(const void*, const Geom&, const Coef<Real<S>::type>&,  \
                                         int, const WallSpec&, double*, cudaStream_t);          \
     template cudaError_t launch_residual<S>(const void*, const Geom&,                          \

@@ -88,6 +88,7 @@ def lib():
             L.lbm_time.argtypes = [P]
             L.lbm_time.restype = C.c_int64
             L.lbm_fields.argtypes = [P, dp, dp, dp, dp, dp]
+            L.lbm_fields_window.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp]
             L.lbm_nusselt_sherwood.argtypes = [P, dp]
             L.lbm_residual.argtypes = [P, dp]
             L.lbm_residual_noalloc.argtypes = [P, C.c_void_p, C.c_int, dp]
@@ -100,7 +101,7 @@ def lib():
             L.lbm_last_error.argtypes = [P]
             L.lbm_last_error.restype = C.c_char_p
             for name in ("lbm_derive_params", "lbm_create", "lbm_create_raw", "lbm_reset", "lbm_step",
-                         "lbm_fields", "lbm_nusselt_sherwood", "lbm_residual",
+                         "lbm_fields", "lbm_fields_window", "lbm_nusselt_sherwood", "lbm_residual",
                          "lbm_residual_noalloc", "lbm_save",
                          "lbm_load", "lbm_get_params"):
                 getattr(L, name).restype = C.c_int
@@ -238,6 +239,12 @@ class Cavity:
         out = {k: np.empty(shp) for k in which}
         args = [_dptr(out.get(k)) for k in ("ux", "uy", "T", "C", "rho")]
         _check(lib().lbm_fields(self.h, *args), self.h)
+        return out
+
+    def fields_window(self, x0, y0, w, h, which=("ux", "uy", "T", "C", "rho")):
+        out = {k: np.empty((h, w)) for k in which}
+        args = [_dptr(out.get(k)) for k in ("ux", "uy", "T", "C", "rho")]
+        _check(lib().lbm_fields_window(self.h, int(x0), int(y0), int(w), int(h), *args), self.h)
         return out
 
     def nusselt_sherwood(self):

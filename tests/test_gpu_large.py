@@ -1,0 +1,107 @@
+"""Full-size and maximum-size grids, checked on sampled windows.
+
+After n steps the state of a node depends only on the initial state within n
+nodes of it, so the oracle run on a small window (with the full grid's lattice
+constants and the full grid's noise keys) reproduces the big grid exactly at
+every node farther than n + 1 nodes from the window's artificial edges (edges
+that coincide with the cavity's walls are the real walls).  The big grid is
+read back window by window (lbm_fields_window)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1708_07525_gb300 import lbm
+from paper_1708_07525_gb300.workloads import CavitySpec, throughput_cavity
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_window(O, spec, x0, y0, w, h, steps):
+    p = O.derive(*spec.args(), varpi=spec.varpi)
+    p.nx, p.ny = w, h                      # constants of the full grid, window extent
+    nfull = spec.nx * spec.ny
+    T = np.empty((h, w))
+    C = np.empty((h, w))
+    for jj in range(h):
+        for ii in range(w):
+            k = (y0 + jj) * spec.nx + (x0 + ii)
+            T[jj, ii] = 0.5 + spec.noise * (2.0 * O.uniform(spec.seed, k) - 1.0)
+            C[jj, ii] = 0.5 + spec.noise * (2.0 * O.uniform(spec.seed, nfull + k) - 1.0)
+    o = O.Oracle(p, seed=spec.seed, noise=spec.noise, T_init=T, C_init=C)
+    o.step(steps)
+    return o.fields()
+
+
+def trusted_mask(spec, x0, y0, w, h, steps):
+    m = np.ones((h, w), bool)
+    d = steps + 1
+    if x0 > 0:
+        m[:, :d] = False
+    if x0 + w < spec.nx:
+        m[:, w - d:] = False
+    if y0 > 0:
+        m[:d, :] = False
+    if y0 + h < spec.ny:
+        m[h - d:, :] = False
+    return m
+
+
+def check_windows(O, cav, spec, windows, steps, tol_rel, keys=("ux", "uy", "T", "C")):
+    for (x0, y0, w, h) in windows:
+        fo = oracle_window(O, spec, x0, y0, w, h, steps)
+        fg = cav.fields_window(x0, y0, w, h)
+        m = trusted_mask(spec, x0, y0, w, h, steps)
+        assert m.sum() > 100
+        for k in keys:
+            a, b = fg[k][m], fo[k][m]
+            if k in ("T", "C"):                 # compare deviations from the reference value
+                a, b = a - 0.5, b - 0.5
+            err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+            assert err <= tol_rel, ((x0, y0), k, err)
+
+
+def test_benchmark_cavity_4096_f32_sampled(oracle_mod):
+    spec = throughput_cavity(4096)
+    steps = 40
+    cav = lbm.Cavity(*spec.args(), precision="f32", seed=spec.seed, noise=spec.noise)
+    cav.step(steps)
+    wins = [(0, 0, 96, 96), (0, 2000, 96, 96), (4000, 4000, 96, 96), (2000, 2000, 96, 96),
+            (4000, 17, 96, 96)]
+    check_windows(oracle_mod, cav, spec, wins, steps, 1e-5)
+
+
+def test_beyond_2_31_nodes_f16_aa_sampled(oracle_mod):
+    """46400^2 = 2.15e9 nodes (> 2^31) in FP16 in-place storage (about 116 GB)."""
+    n = 46400
+    spec = CavitySpec(n, n, Ra=1e5, Da=1e-3, eps=0.4, Le=5.0, N=-1.0, seed=9, noise=0.05)
+    steps = 6
+    cav = lbm.Cavity(*spec.args(), precision="f16", layout="aa", seed=spec.seed, noise=spec.noise)
+    assert cav.device_bytes() > 100e9
+    cav.step(steps)
+    wins = [(0, 0, 48, 48), (n - 48, n - 48, 48, 48), (n // 2, n - 48, 48, 48),
+            (n - 48, 12345, 48, 48), (31000, 40000, 48, 48)]
+    # FP16 storage (11 significant bits, stochastic rounding) against FP64
+    check_windows(oracle_mod, cav, spec, wins, steps, 2e-2, keys=("T", "C"))
+    check_windows(oracle_mod, cav, spec, wins[:2], steps, 5e-2, keys=("ux", "uy"))
+    cav.close()
+
+
+def test_window_and_empty_step_edges():
+    spec = CavitySpec(37, 29, Ra=1e4, Da=1e-2, eps=0.6, Le=2.0, N=1.0, seed=3)
+    cav = lbm.Cavity(*spec.args(), precision="f32", seed=spec.seed)
+    before = cav.fields()
+    cav.step(0)                                    # an empty step is a no-op
+    assert cav.t == 0
+    after = cav.fields()
+    for k in before:
+        assert np.array_equal(before[k], after[k])
+    cav.step(17)
+    full = cav.fields()
+    win = cav.fields_window(5, 3, 20, 11)
+    for k in full:
+        assert np.array_equal(win[k], full[k][3:14, 5:25])
+    for bad in ((-1, 0, 5, 5), (30, 0, 10, 5), (0, 0, 0, 5), (0, 25, 5, 5)):
+        with pytest.raises(lbm.LbmError) as ei:
+            cav.fields_window(*bad)
+        assert ei.value.status == lbm.ERR_INVALID

@@ -182,3 +182,14 @@ def test_residual_and_divergence_flag():
     with pytest.raises(lbm.LbmError) as ei:
         bad.nusselt_sherwood()
     assert ei.value.status == lbm.ERR_DIVERGED
+
+
+def test_precision_study_cavity_fp64_against_oracle(oracle_mod):
+    """The 1024^2 precision-study cavity (Ra 1e5, Da 1e-2, eps 0.6, Le 10, N 2) in FP64
+    against the oracle over a fixed 200 steps: the FP64 GPU path serves as the
+    steady-state reference for the storage-precision study."""
+    from paper_1708_07525_gb300.workloads import PRECISION_STUDY
+    gpu, ora = make_pair(oracle_mod, PRECISION_STUDY, "f64", "ab")
+    gpu.step(200)
+    ora.step(200)
+    compare(gpu, ora, 1e-12, nush_tol=1e-12)
