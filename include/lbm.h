@@ -116,6 +116,9 @@ typedef struct {
     double Tw[4], Cw[4];        /* Dirichlet wall values by side: [0] left (x = 0),
                                    [1] right (x = nx), [2] bottom (y = 0), [3] top (y = ny) */
     int wall_lr, wall_tb;       /* LBM_WALL_* for g and h on left/right, bottom/top */
+    int model_a;                /* 0: the paper's equilibria (Eqs. 24-25); 1: the coupled
+                                   "model A" equilibria of Eqs. 30-31 (a negative control; with
+                                   it, Eq. 32 relates zeta, eta to the diffusivities) */
 } lbm_params;
 
 /* Parameter mapping of Sec. 4 and 4.1 (L = nx, c_s^2 = 1/3, U = Ma c_s,
@@ -128,6 +131,13 @@ typedef struct {
 lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, double Pr,
                              double Le, double N, double J, double sigma, double Ma,
                              double varpi, lbm_params* out);
+
+/* Switch parameters from lbm_derive_params() to the coupled "model A" equilibria
+ * (Eqs. 30-31) with the same effective diffusivities: by Eq. 32,
+ * 1/zeta_a = 1/2 + alpha_e / (sigma c_sT^2), 1/eta_D = 1/2 + D_e / (eps c_sT^2).
+ * A negative control: the paper's model (Eqs. 24-25, 29) keeps these independent
+ * of sigma and eps.  LBM_ERR_INVALID if a rate leaves (0, 2) or p is NULL. */
+lbm_status lbm_params_model_a(lbm_params* p);
 
 /* Create a cavity at t = 0: u = 0, rho = rho0, T = C = 1/2 plus uniform noise
  * of amplitude opt->noise drawn by SplitMix64 (Steele, Lea & Flood 2014) with

@@ -135,6 +135,7 @@ int or_derive(or_params* p)
     p->Tw[0] = 1.0; p->Tw[1] = 0.0;
     p->Cw[0] = 1.0; p->Cw[1] = 0.0;
     p->Gx = 0.0;
+    p->model_a = 0;
     for (int k = 0; k < 9; ++k) if (!(p->s[k] > 0.0 && p->s[k] < 2.0)) return 2;
     for (int k = 0; k < 5; ++k)
         if (!(p->zeta[k] > 0.0 && p->zeta[k] < 2.0) || !(p->eta[k] > 0.0 && p->eta[k] < 2.0))
@@ -231,8 +232,9 @@ static void collide_d2q5(const or_params* p, const double rates[5], double cap, 
         n[k] = 0;
         for (int i = 0; i < 5; ++i) n[k] += N5[k][i] * d[i];
     }
-    /* Eqs. 24/25: modified equilibrium moments */
+    /* Eqs. 24/25: modified equilibrium moments; model A: Eqs. 30/31 */
     double neq[5] = {cap * Phi, ux * Phi, uy * Phi, -4.0 * cap * Phi + 5.0 * varpi * Phi, 0.0};
+    if (p->model_a) neq[3] = (-4.0 + 5.0 * varpi) * cap * Phi;
     /* n* = n - Theta (n - n_eq) + (I - Theta/2) S */
     double ns[5];
     for (int k = 0; k < 5; ++k)
@@ -340,12 +342,21 @@ or_state* or_create(const or_params* p, uint64_t seed, double noise, const doubl
                               : p->C0 + noise * (2.0 * or_uniform(seed, n + x) - 1.0);
             /* Eq. 20 at rho = rho0, u = 0 */
             for (int q = 0; q < 9; ++q) s->f[q * n + x] = W9[q] * p->rho0;
-            /* Eq. 28 at u = 0 */
-            s->g[x] = p->sigma * T - varpi * T;
-            s->h[x] = p->eps * C - varpi * C;
-            for (int q = 1; q < 5; ++q) {
-                s->g[q * n + x] = varpi / 4 * T;
-                s->h[q * n + x] = varpi / 4 * C;
+            /* Eq. 28 at u = 0; model A: g_i^eq = w~_i T (sigma + e_i.u / c_sT^2) at u = 0 */
+            if (!p->model_a) {
+                s->g[x] = p->sigma * T - varpi * T;
+                s->h[x] = p->eps * C - varpi * C;
+                for (int q = 1; q < 5; ++q) {
+                    s->g[q * n + x] = varpi / 4 * T;
+                    s->h[q * n + x] = varpi / 4 * C;
+                }
+            } else {
+                s->g[x] = (1.0 - varpi) * p->sigma * T;
+                s->h[x] = (1.0 - varpi) * p->eps * C;
+                for (int q = 1; q < 5; ++q) {
+                    s->g[q * n + x] = varpi / 4 * p->sigma * T;
+                    s->h[q * n + x] = varpi / 4 * p->eps * C;
+                }
             }
         }
     /* history = (T u, C u) of the initial state */
@@ -416,10 +427,12 @@ void or_step(or_state* s, long nsteps)
                     int lr = (ti < 0 || ti >= nx);           /* left/right wall link */
                     int type = lr ? p->scalar_lr : p->scalar_tb;
                     if (type == OR_DIRICHLET) {
-                        /* anti-bounce-back: g_opp(x) = -g*_q(x) + 2 w~ T_w */
+                        /* anti-bounce-back: g_opp(x) = -g*_q(x) + g_q^eq(T_w) + g_opp^eq(T_w),
+                         * = 2 w~ T_w (Eq. 28), = 2 w~ sigma T_w (model A) */
                         int side = lr ? (ti < 0 ? 0 : 1) : (tj < 0 ? 0 : 1);
-                        s->g2[opp[q] * n + x] = -gs[q] + 2.0 * wt_axis * p->Tw[side];
-                        s->h2[opp[q] * n + x] = -hs[q] + 2.0 * wt_axis * p->Cw[side];
+                        double kg = p->model_a ? p->sigma : 1.0, kh = p->model_a ? p->eps : 1.0;
+                        s->g2[opp[q] * n + x] = -gs[q] + 2.0 * wt_axis * kg * p->Tw[side];
+                        s->h2[opp[q] * n + x] = -hs[q] + 2.0 * wt_axis * kh * p->Cw[side];
                     } else {
                         /* adiabatic / impermeable: plain bounce-back */
                         s->g2[opp[q] * n + x] = gs[q];

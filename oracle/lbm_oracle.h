@@ -15,6 +15,8 @@
  *   - Brinkman-Forchheimer total force and buoyancy            Sec. 2, Eqs. 5-7
  *   - D2Q5 temperature / concentration MRT collisions with the
  *     modified equilibrium moments and source terms            Sec. 3.2, Eqs. 21-27
+ *   - optionally the coupled "model A" equilibria (negative
+ *     control of Sec. 3.2)                                     Eqs. 30-32
  *   - streaming in velocity space                              Eq. 11
  *   - Nusselt / Sherwood numbers                               Sec. 4.1, Eq. 38
  *   - parameter mapping from Ra, Pr, Le, Da, Ma                Sec. 4 and 4.1
@@ -26,7 +28,7 @@
  *   - the time derivative of T*u in Eq. 27 is the explicit backward
  *     difference the paper suggests (Sec. 3.2), with the history initialised
  *     to T*u of the initial state, so the source vanishes at the first step.
- *   - initial noise: SplitMix64 (Steele, Lea & Flood 2014), see or_noise().
+ *   - initial noise: SplitMix64 (Steele, Lea & Flood 2014), see or_uniform().
  *
  * Parity status: every function here is pinned by tests under tests/
  * (identities between the paper's moment- and velocity-space forms,
@@ -57,6 +59,8 @@ typedef struct {
     int scalar_lr, scalar_tb;   /* OR_DIRICHLET / OR_ADIABATIC for g and h */
     double Tw[2], Cw[2];        /* Dirichlet values, [0]=left (x=0), [1]=right (x=nx) */
     double Gx;                  /* constant external body force along x (enters as eps*G) */
+    int model_a;                /* 1: the coupled equilibria of Eqs. 30-31 ("model A"), whose
+                                   diffusivities follow Eq. 32; 0: Eqs. 24-25 (the paper's model) */
 } or_params;
 
 typedef struct or_state or_state;

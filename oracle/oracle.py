@@ -44,6 +44,7 @@ class Params(C.Structure):
         ("scalar_lr", C.c_int), ("scalar_tb", C.c_int),
         ("Tw", C.c_double * 2), ("Cw", C.c_double * 2),
         ("Gx", C.c_double),
+        ("model_a", C.c_int),
     ]
 
 
@@ -104,6 +105,19 @@ def derive(nx, ny, Ra, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, Ma=0.1, varpi=0.4) 
     rc = lib().or_derive(C.byref(p))
     if rc != 0:
         raise ValueError(f"invalid parameters (or_derive returned {rc})")
+    return p
+
+
+def to_model_a(p: Params) -> Params:
+    """Switch p to the coupled equilibria of Eqs. 30-31 keeping the same effective
+    diffusivities: by Eq. 32 alpha_e = sigma c_sT^2 (1/zeta_a - 1/2) and
+    D_e = eps c_sT^2 (1/eta_D - 1/2), so the rates are re-derived from Eq. 29's."""
+    za, eD = p.zeta[1], p.eta[1]
+    za_a = 1.0 / (0.5 + (1.0 / za - 0.5) / p.sigma)
+    eD_a = 1.0 / (0.5 + (1.0 / eD - 0.5) / p.eps)
+    p.zeta[1] = p.zeta[2] = za_a
+    p.eta[1] = p.eta[2] = eD_a
+    p.model_a = 1
     return p
 
 

@@ -67,12 +67,16 @@ Coef<R> make_coef(const lbm_params& P) {
     c.s5 = (R)P.s[5]; c.s6 = (R)P.s[6]; c.s7 = (R)P.s[7]; c.s8 = (R)P.s[8];
     c.za1 = (R)P.zeta[1]; c.za2 = (R)P.zeta[2]; c.za3 = (R)P.zeta[3]; c.za4 = (R)P.zeta[4];
     c.ed1 = (R)P.eta[1]; c.ed2 = (R)P.eta[2]; c.ed3 = (R)P.eta[3]; c.ed4 = (R)P.eta[4];
-    c.c3T = (R)(5.0 * P.varpi - 4.0 * P.sigma);             // Eq. 24
-    c.c3C = (R)(5.0 * P.varpi - 4.0 * eps);                 // Eq. 25
+    // Eqs. 24 / 25 (model A: Eqs. 30 / 31): n_eq,3 = c3 Phi
+    c.c3T = (R)(P.model_a ? (5.0 * P.varpi - 4.0) * P.sigma : 5.0 * P.varpi - 4.0 * P.sigma);
+    c.c3C = (R)(P.model_a ? (5.0 * P.varpi - 4.0) * eps : 5.0 * P.varpi - 4.0 * eps);
     const double w = 0.25 * P.varpi;                        // w~_1..4 (Sec. 3.2)
+    // anti-bounce-back constant g_q^eq + g_opp^eq at the wall value: 2 w~ Phi_w (Eq. 28),
+    // 2 w~ sigma T_w / 2 w~ eps C_w for model A; in deviations from Phi0
+    const double kg = P.model_a ? P.sigma : 1.0, kh = P.model_a ? eps : 1.0;
     for (int s = 0; s < 4; ++s) {
-        c.wallT[s] = (R)(2.0 * w * (P.Tw[s] - P.T0));
-        c.wallC[s] = (R)(2.0 * w * (P.Cw[s] - P.C0));
+        c.wallT[s] = (R)(2.0 * w * kg * (P.Tw[s] - P.T0));
+        c.wallC[s] = (R)(2.0 * w * kh * (P.Cw[s] - P.C0));
     }
     c.dirichlet_mask = (P.wall_lr == LBM_WALL_DIRICHLET ? 3 : 0) |
                        (P.wall_tb == LBM_WALL_DIRICHLET ? 12 : 0);
@@ -101,6 +105,7 @@ const char* check_params(const lbm_params& P) {
             return "a scalar relaxation rate lies outside (0, 2)";
     if (P.wall_lr != LBM_WALL_DIRICHLET && P.wall_lr != LBM_WALL_ADIABATIC) return "bad wall_lr";
     if (P.wall_tb != LBM_WALL_DIRICHLET && P.wall_tb != LBM_WALL_ADIABATIC) return "bad wall_tb";
+    if (P.model_a != 0 && P.model_a != 1) return "model_a must be 0 or 1";
     if ((double)P.nx * (double)P.ny > 4.0e9) return "grid too large";
     return nullptr;
 }
@@ -250,6 +255,7 @@ lbm_status do_init(lbm_ctx* c, const double* T_host, const double* C_host, uint6
     I.sigma = c->P.sigma;
     I.eps = c->P.eps;
     I.varpi = c->P.varpi;
+    I.model_a = c->P.model_a;
     const size_t n = c->nodes();
     cudaError_t e = cudaSuccess;
     if (T_host) {
@@ -355,6 +361,28 @@ lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, do
         return LBM_ERR_INVALID;
     }
     *out = P;
+    return LBM_OK;
+}
+
+lbm_status lbm_params_model_a(lbm_params* p) {
+    if (!p || p->model_a) {
+        set_global_error("lbm_params_model_a: NULL parameters, or already model A");
+        return LBM_ERR_INVALID;
+    }
+    // Eq. 29 -> alpha_e, D_e; Eq. 32 -> the model-A rates
+    const double csT2 = 0.5 * p->varpi;
+    const double alpha_e = csT2 * (1.0 / p->zeta[1] - 0.5);
+    const double D_e = csT2 * (1.0 / p->eta[1] - 0.5);
+    lbm_params q = *p;
+    q.zeta[1] = q.zeta[2] = 1.0 / (0.5 + alpha_e / (p->sigma * csT2));
+    q.eta[1] = q.eta[2] = 1.0 / (0.5 + D_e / (p->eps * csT2));
+    q.model_a = 1;
+    const char* bad = check_params(q);
+    if (bad) {
+        set_global_error("lbm_params_model_a: %s", bad);
+        return LBM_ERR_INVALID;
+    }
+    *p = q;
     return LBM_OK;
 }
 

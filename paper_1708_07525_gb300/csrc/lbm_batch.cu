@@ -411,6 +411,7 @@ lbm_status init_slot(lbm_batch* b, int k) {
     I.sigma = s.P.sigma;
     I.eps = s.P.eps;
     I.varpi = s.P.varpi;
+    I.model_a = s.P.model_a;
     const Coef<float> c = coef_from(s.P, b->sr);
     const bool pull = b->layout == LBM_AB_PULL;
     void* buf0 = b->slot_buf(s, 0);

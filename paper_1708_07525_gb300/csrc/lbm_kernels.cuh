@@ -209,8 +209,10 @@ __device__ __forceinline__ void initial_TC(const InitSpec& I, const Geom& G, int
     }
 }
 
-// Deviation of the D2Q5 rest equilibrium of Eq. 28 at u = 0 for Phi' = Phi - Phi0.
-__device__ __forceinline__ double eq5_dev(int q, double cap, double varpi, double Pp) {
+// Deviation of the D2Q5 rest equilibrium of Eq. 28 at u = 0 for Phi' = Phi - Phi0
+// (model A: w~_q cap Phi', from the velocity-space form of Eqs. 30-31).
+__device__ __forceinline__ double eq5_dev(int q, double cap, double varpi, double Pp, int model_a) {
+    if (model_a) return (q == 0 ? 1.0 - varpi : 0.25 * varpi) * cap * Pp;
     return q == 0 ? (cap - varpi) * Pp : 0.25 * varpi * Pp;
 }
 
@@ -235,20 +237,20 @@ __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restr
     for (int q = 0; q < 5; ++q) {
         double vg, vh;
         if (!PULL) {
-            vg = eq5_dev(q, I.sigma, I.varpi, Tp);
-            vh = eq5_dev(q, I.eps, I.varpi, Cp);
+            vg = eq5_dev(q, I.sigma, I.varpi, Tp, I.model_a);
+            vh = eq5_dev(q, I.eps, I.varpi, Cp, I.model_a);
         } else {
             const int ti = i + ex_of(q), tj = j + ey_of(q);
             if ((unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny) {
                 double Tn, Cn;
                 initial_TC(I, G, ti, tj, Tn, Cn);
-                vg = eq5_dev(q, I.sigma, I.varpi, Tn);
-                vh = eq5_dev(q, I.eps, I.varpi, Cn);
+                vg = eq5_dev(q, I.sigma, I.varpi, Tn, I.model_a);
+                vh = eq5_dev(q, I.eps, I.varpi, Cn, I.model_a);
             } else {
                 // pulled back at y along opp(q) through the wall ahead of q
                 const int o = opp_of(q), side = pull_side(o);
-                const double wg = eq5_dev(o, I.sigma, I.varpi, Tp);
-                const double wh = eq5_dev(o, I.eps, I.varpi, Cp);
+                const double wg = eq5_dev(o, I.sigma, I.varpi, Tp, I.model_a);
+                const double wh = eq5_dev(o, I.eps, I.varpi, Cp, I.model_a);
                 const bool dir = (c.dirichlet_mask >> side) & 1;
                 vg = dir ? (double)c.wallT[side] - wg : wg;
                 vh = dir ? (double)c.wallC[side] - wh : wh;
@@ -263,8 +265,8 @@ __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restr
     for (int q = 0; q < 9; ++q) f[q] = R(0);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        g[q] = (R)eq5_dev(q, I.sigma, I.varpi, Tp);
-        h[q] = (R)eq5_dev(q, I.eps, I.varpi, Cp);
+        g[q] = (R)eq5_dev(q, I.sigma, I.varpi, Tp, I.model_a);
+        h[q] = (R)eq5_dev(q, I.eps, I.varpi, Cp, I.model_a);
     }
     Macro<R> M = macro(c, f, g, h);
     R hv[4];

@@ -26,6 +26,7 @@ struct InitSpec {
     uint64_t seed;
     double noise;
     double T0, C0, sigma, eps, varpi;
+    int model_a;            // equilibria of Eqs. 30-31 instead of Eqs. 24-25
 };
 
 struct WallSpec {

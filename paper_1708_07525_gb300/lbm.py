@@ -59,7 +59,7 @@ class lbm_params(C.Structure):
         ("gbT", C.c_double), ("gbC", C.c_double), ("Gx", C.c_double), ("T0", C.c_double),
         ("C0", C.c_double), ("s", C.c_double * 9), ("zeta", C.c_double * 5),
         ("eta", C.c_double * 5), ("Tw", C.c_double * 4), ("Cw", C.c_double * 4),
-        ("wall_lr", C.c_int), ("wall_tb", C.c_int),
+        ("wall_lr", C.c_int), ("wall_tb", C.c_int), ("model_a", C.c_int),
     ]
 
 
@@ -83,6 +83,7 @@ def lib():
                                                                      C.POINTER(C.c_void_p)]
             L.lbm_create_raw.argtypes = [C.POINTER(lbm_params), C.POINTER(lbm_options),
                                          C.POINTER(C.c_void_p)]
+            L.lbm_params_model_a.argtypes = [C.POINTER(lbm_params)]
             L.lbm_reset.argtypes = [P, dp, dp, C.c_uint64, C.c_double]
             L.lbm_step.argtypes = [P, C.c_int64]
             L.lbm_time.argtypes = [P]
@@ -100,7 +101,8 @@ def lib():
             L.lbm_destroy.argtypes = [P]
             L.lbm_last_error.argtypes = [P]
             L.lbm_last_error.restype = C.c_char_p
-            for name in ("lbm_derive_params", "lbm_create", "lbm_create_raw", "lbm_reset", "lbm_step",
+            for name in ("lbm_derive_params", "lbm_params_model_a", "lbm_create", "lbm_create_raw",
+                         "lbm_reset", "lbm_step",
                          "lbm_fields", "lbm_fields_window", "lbm_nusselt_sherwood", "lbm_residual",
                          "lbm_residual_noalloc", "lbm_save",
                          "lbm_load", "lbm_get_params"):
@@ -154,6 +156,11 @@ def lbm_derive_params(nx, ny, Ra, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, Ma=0.0, 
     p = lbm_params()
     _check(lib().lbm_derive_params(lbm_grid(int(nx), int(ny)), Ra, Da, eps, Pr, Le, N, J, sigma,
                                    Ma, varpi, C.byref(p)))
+    return p
+
+
+def lbm_params_model_a(p: lbm_params) -> lbm_params:
+    _check(lib().lbm_params_model_a(C.byref(p)))
     return p
 
 

@@ -193,3 +193,17 @@ def test_precision_study_cavity_fp64_against_oracle(oracle_mod):
     gpu.step(200)
     ora.step(200)
     compare(gpu, ora, 1e-12, nush_tol=1e-12)
+
+
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_model_a_f64_against_oracle(oracle_mod, layout):
+    """The model-A equilibria (Eqs. 30-32) on the GPU against the oracle's."""
+    spec = SMALL[3]
+    p = lbm.lbm_params_model_a(lbm.lbm_derive_params(*spec.args()))
+    po = oracle_mod.to_model_a(oracle_mod.derive(*spec.args()))
+    assert abs(p.zeta[1] - po.zeta[1]) < 1e-14 and abs(p.eta[1] - po.eta[1]) < 1e-14
+    gpu = lbm.Cavity(params=p, precision="f64", layout=layout, seed=spec.seed, noise=spec.noise)
+    ora = oracle_mod.Oracle(po, seed=spec.seed, noise=spec.noise)
+    gpu.step(1000)
+    ora.step(1000)
+    compare(gpu, ora, 1e-12, nush_tol=1e-11)

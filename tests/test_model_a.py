@@ -1,0 +1,89 @@
+"""Model A (Eqs. 30-32, the coupled equilibria the paper argues against) as a
+negative control.
+
+* Its collision equals the velocity-space form with g_i^eq = w~_i T (sigma +
+  e_i . u / c_sT^2) (the velocity-space equilibria stated with Eqs. 30-31).
+* Steady state, Le = 1, identical wall data: the paper's model gives Nu = Sh
+  exactly (tested in test_oracle_physics), model A with eps != sigma does not
+  (its discrete T and C equations differ), while at eps = sigma = 1 the two
+  models are the same scheme.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from test_oracle_collision import NM, EX, EY, velocity_newton
+
+
+def geq_a(p, cap, Phi, ux, uy):
+    wt = np.array([1 - p.varpi] + [p.varpi / 4] * 4)
+    return wt * Phi * (cap + (EX[:5] * ux + EY[:5] * uy) / p.csT2)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_model_a_collision_velocity_space(oracle_mod, seed):
+    O = oracle_mod
+    rng = np.random.default_rng(100 + seed)
+    p = O.derive(32, 32, 1e4, 1e-2, rng.uniform(0.3, 1.0), 1, rng.uniform(0.5, 5), 1.0,
+                 sigma=rng.uniform(0.5, 2))
+    O.to_model_a(p)
+    assert p.model_a == 1
+    ux, uy = rng.uniform(-0.05, 0.05, 2)
+    T, C = rng.uniform(0, 1, 2)
+    W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    f = W9 * (1 + rng.uniform(-0.05, 0.05, 9))
+    g = geq_a(p, p.sigma, T, ux, uy) + rng.uniform(-0.01, 0.01, 5)
+    h = geq_a(p, p.eps, C, ux, uy) + rng.uniform(-0.01, 0.01, 5)
+    hist = rng.uniform(-0.02, 0.02, 4)
+    fs, gs, hs, _, mac = O.collide_node(p, f, g, h, hist)
+    Tm, Cm = g.sum() / p.sigma, h.sum() / p.eps
+    u = velocity_newton(p, f, Tm, Cm)
+    wt = np.array([1 - p.varpi] + [p.varpi / 4] * 4)
+    Ni = np.linalg.inv(NM)
+    for d, ds, cap, Phi, rates, X in ((g, gs, p.sigma, Tm, p.zeta, hist[:2]),
+                                      (h, hs, p.eps, Cm, p.eta, hist[2:])):
+        Th = np.diag(np.array(rates[:]))
+        Xv = (Phi * u[0] - X[0], Phi * u[1] - X[1])
+        Sv = wt * (EX[:5] * Xv[0] + EY[:5] * Xv[1]) / p.csT2
+        ref = d - Ni @ Th @ NM @ (d - geq_a(p, cap, Phi, u[0], u[1])) \
+            + Ni @ (np.eye(5) - Th / 2) @ NM @ Sv
+        np.testing.assert_allclose(ds, ref, rtol=0, atol=2e-15)
+
+
+def _steady(O, p, tol=1e-11):
+    o = O.Oracle(p, seed=1, noise=1e-3)
+    prev = None
+    for _ in range(200):
+        o.step(2000)
+        fl = o.fields()
+        if prev is not None and max(np.abs(fl[k] - prev[k]).max() / np.abs(fl[k]).max()
+                                    for k in ("T", "C")) < tol:
+            break
+        prev = fl
+    return o
+
+
+def test_model_a_breaks_nu_equals_sh(oracle_mod):
+    O = oracle_mod
+    O.set_threads(os.cpu_count() or 1)
+    p = O.derive(12, 12, 2e3, 1e-1, 0.6, 1, 1, 1, sigma=1.0)
+    present = _steady(O, p).nusselt_sherwood()
+    assert abs(present[0] - present[1]) < 1e-8
+    pa = O.to_model_a(O.derive(12, 12, 2e3, 1e-1, 0.6, 1, 1, 1, sigma=1.0))
+    model_a = _steady(O, pa).nusselt_sherwood()
+    gap = abs(model_a[0] - model_a[1]) / model_a[0]
+    assert gap > 1e-5, gap                      # T and C no longer coincide
+    assert abs(model_a[0] - present[0]) / present[0] < 2e-2   # same physics, nearby values
+
+
+def test_model_a_equals_present_model_at_unit_capacities(oracle_mod):
+    O = oracle_mod
+    p0 = O.derive(10, 9, 5e3, 1e-2, 1.0, 1, 2, 1.5, sigma=1.0)
+    p1 = O.to_model_a(O.derive(10, 9, 5e3, 1e-2, 1.0, 1, 2, 1.5, sigma=1.0))
+    a, b = O.Oracle(p0, seed=2, noise=0.01), O.Oracle(p1, seed=2, noise=0.01)
+    a.step(300)
+    b.step(300)
+    fa, fb = a.fields(), b.fields()
+    for k in ("ux", "uy", "T", "C"):
+        np.testing.assert_allclose(fa[k], fb[k], rtol=0, atol=1e-13)   # rounding order only
