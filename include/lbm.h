@@ -116,6 +116,9 @@ typedef struct {
     double Tw[4], Cw[4];        /* Dirichlet wall values by side: [0] left (x = 0),
                                    [1] right (x = nx), [2] bottom (y = 0), [3] top (y = ny) */
     int wall_lr, wall_tb;       /* LBM_WALL_* for g and h on left/right, bottom/top */
+    double uw[4][2];            /* velocity (x, y) of each wall side (same order as Tw);
+                                   0 = resting no-slip wall; a moving lid bounces populations
+                                   back with the momentum 2 w_i rho0 (e_i . u_w) / c_s^2 */
     int model_a;                /* 0: the paper's equilibria (Eqs. 24-25); 1: the coupled
                                    "model A" equilibria of Eqs. 30-31 (a negative control; with
                                    it, Eq. 32 relates zeta, eta to the diffusivities) */
@@ -131,6 +134,15 @@ typedef struct {
 lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, double Pr,
                              double Le, double N, double J, double sigma, double Ma,
                              double varpi, lbm_params* out);
+
+/* Parameter mapping of the lid-driven porous cavity of Sec. 4.3: top wall moving
+ * with U0 along +x, top T = C = 1 and bottom T = C = 0 (Dirichlet), left and right
+ * walls adiabatic; Re = L U0 / nu with 1/s_nu = 1/2 + J L U0 / (c_s^2 Re);
+ * Gr = g beta_T dT L^3 / nu^2; Pr, Le, N, Da, eps, sigma as in lbm_derive_params;
+ * L = nx.  U0 <= 0 -> 0.1, varpi <= 0 -> 0.4. */
+lbm_status lbm_derive_params_lid(lbm_grid grid, double Re, double Gr, double Da, double eps,
+                                 double Pr, double Le, double N, double J, double sigma,
+                                 double U0, double varpi, lbm_params* out);
 
 /* Switch parameters from lbm_derive_params() to the coupled "model A" equilibria
  * (Eqs. 30-31) with the same effective diffusivities: by Eq. 32,
@@ -188,6 +200,11 @@ lbm_status lbm_fields_window(lbm_ctx* ctx, int x0, int y0, int w, int h, double*
  * right; Nu(y) = -L dT/dx / dT with L = nx; the mean is over the ny rows.
  * Synchronises the stream.  LBM_ERR_DIVERGED if a result is not finite. */
 lbm_status lbm_nusselt_sherwood(lbm_ctx* ctx, double out[4]);
+
+/* Mean Nu and Sh on the bottom and top walls: the wall-normal gradient (same
+ * one-sided stencil) times L = ny over (top value - bottom value), averaged over
+ * the nx columns; out = {Nu_B, Sh_B, Nu_T, Sh_T}, FP64.  Synchronises. */
+lbm_status lbm_nusselt_sherwood_tb(lbm_ctx* ctx, double out[4]);
 
 /* Steady-state residual: r = max over phi in {u_x, u_y, T, C} of
  * max|phi_now - phi_snap| / max|phi_now|, where phi_snap is the snapshot of

@@ -132,8 +132,9 @@ int or_derive(or_params* p)
     memcpy(p->eta, e, sizeof e);
     p->scalar_lr = OR_DIRICHLET;
     p->scalar_tb = OR_ADIABATIC;
-    p->Tw[0] = 1.0; p->Tw[1] = 0.0;
-    p->Cw[0] = 1.0; p->Cw[1] = 0.0;
+    p->Tw[0] = 1.0; p->Tw[1] = 0.0; p->Tw[2] = 0.5; p->Tw[3] = 0.5;
+    p->Cw[0] = 1.0; p->Cw[1] = 0.0; p->Cw[2] = 0.5; p->Cw[3] = 0.5;
+    memset(p->uw, 0, sizeof p->uw);
     p->Gx = 0.0;
     p->model_a = 0;
     for (int k = 0; k < 9; ++k) if (!(p->s[k] > 0.0 && p->s[k] < 2.0)) return 2;
@@ -410,10 +411,16 @@ void or_step(or_state* s, long nsteps)
                     int ti = i + EX[q], tj = j + EY[q];
                     if (p->periodic_x) ti = (ti + nx) % nx;
                     if (p->periodic_y) tj = (tj + ny) % ny;
-                    if (ti >= 0 && ti < nx && tj >= 0 && tj < ny)
+                    if (ti >= 0 && ti < nx && tj >= 0 && tj < ny) {
                         s->f2[q * n + (size_t)tj * nx + ti] = fs[q];
-                    else
-                        s->f2[opp[q] * n + x] = fs[q];       /* no-slip bounce-back */
+                    } else {
+                        /* halfway bounce-back off a wall moving with u_w (a resting wall:
+                         * no-slip): f_opp(x) = f*_q(x) - 2 w_q rho0 (e_q . u_w) / c_s^2.
+                         * A link through a corner takes the bottom / top wall. */
+                        int side = (tj < 0 || tj >= ny) ? (tj < 0 ? 2 : 3) : (ti < 0 ? 0 : 1);
+                        double eu = EX[q] * p->uw[side][0] + EY[q] * p->uw[side][1];
+                        s->f2[opp[q] * n + x] = fs[q] - 2.0 * W9[q] * p->rho0 * eu / p->cs2;
+                    }
                 }
                 for (int q = 0; q < 5; ++q) {
                     int ti = i + EX[q], tj = j + EY[q];
@@ -429,7 +436,7 @@ void or_step(or_state* s, long nsteps)
                     if (type == OR_DIRICHLET) {
                         /* anti-bounce-back: g_opp(x) = -g*_q(x) + g_q^eq(T_w) + g_opp^eq(T_w),
                          * = 2 w~ T_w (Eq. 28), = 2 w~ sigma T_w (model A) */
-                        int side = lr ? (ti < 0 ? 0 : 1) : (tj < 0 ? 0 : 1);
+                        int side = lr ? (ti < 0 ? 0 : 1) : (tj < 0 ? 2 : 3);
                         double kg = p->model_a ? p->sigma : 1.0, kh = p->model_a ? p->eps : 1.0;
                         s->g2[opp[q] * n + x] = -gs[q] + 2.0 * wt_axis * kg * p->Tw[side];
                         s->h2[opp[q] * n + x] = -hs[q] + 2.0 * wt_axis * kh * p->Cw[side];
@@ -495,6 +502,31 @@ void or_nusselt_sherwood(const or_state* s, double out[4])
         shR += -nx * dCdx_R / dC;
     }
     out[0] = nuL / ny; out[1] = shL / ny; out[2] = nuR / ny; out[3] = shR / ny;
+    free(T);
+    free(C);
+}
+
+void or_nusselt_sherwood_tb(const or_state* s, double out[4])
+{
+    const or_params* p = &s->p;
+    int nx = p->nx, ny = p->ny;
+    size_t n = s->n;
+    double* T = (double*)malloc(n * sizeof(double));
+    double* C = (double*)malloc(n * sizeof(double));
+    or_fields(s, NULL, NULL, T, C, NULL);
+    double dT = p->Tw[3] - p->Tw[2], dC = p->Cw[3] - p->Cw[2];
+    double nuB = 0, shB = 0, nuT = 0, shT = 0;
+    for (int i = 0; i < nx; ++i) {
+        double T0 = T[i], T1 = T[(size_t)nx + i];
+        double C0 = C[i], C1 = C[(size_t)nx + i];
+        double Tn = T[(size_t)(ny - 1) * nx + i], Tm = T[(size_t)(ny - 2) * nx + i];
+        double Cn = C[(size_t)(ny - 1) * nx + i], Cm = C[(size_t)(ny - 2) * nx + i];
+        nuB += ny * (-8.0 * p->Tw[2] + 9.0 * T0 - T1) / 3.0 / dT;
+        shB += ny * (-8.0 * p->Cw[2] + 9.0 * C0 - C1) / 3.0 / dC;
+        nuT += ny * (8.0 * p->Tw[3] - 9.0 * Tn + Tm) / 3.0 / dT;
+        shT += ny * (8.0 * p->Cw[3] - 9.0 * Cn + Cm) / 3.0 / dC;
+    }
+    out[0] = nuB / nx; out[1] = shB / nx; out[2] = nuT / nx; out[3] = shT / nx;
     free(T);
     free(C);
 }

@@ -57,7 +57,9 @@ typedef struct {
     /* boundary and test knobs */
     int periodic_x, periodic_y;
     int scalar_lr, scalar_tb;   /* OR_DIRICHLET / OR_ADIABATIC for g and h */
-    double Tw[2], Cw[2];        /* Dirichlet values, [0]=left (x=0), [1]=right (x=nx) */
+    double Tw[4], Cw[4];        /* Dirichlet values by side: [0] left (x = 0), [1] right (x = nx),
+                                   [2] bottom (y = 0), [3] top (y = ny) */
+    double uw[4][2];            /* wall velocity (x, y) by side; 0 for resting walls */
     double Gx;                  /* constant external body force along x (enters as eps*G) */
     int model_a;                /* 1: the coupled equilibria of Eqs. 30-31 ("model A"), whose
                                    diffusivities follow Eq. 32; 0: Eqs. 24-25 (the paper's model) */
@@ -86,6 +88,9 @@ void or_fields(const or_state* s, double* ux, double* uy, double* T, double* C, 
 
 /* Mean Nu and Sh on the left and right walls (Eq. 38), out = {Nu_L, Sh_L, Nu_R, Sh_R}. */
 void or_nusselt_sherwood(const or_state* s, double out[4]);
+/* Mean Nu and Sh on the bottom and top walls, out = {Nu_B, Sh_B, Nu_T, Sh_T}: the wall-normal
+ * gradient times L = ny over (Phi_top - Phi_bottom), averaged over the nx columns. */
+void or_nusselt_sherwood_tb(const or_state* s, double out[4]);
 
 /* Copy the distributions out / in, layout [q][ny][nx]; hist is [4][ny][nx] =
  * (T u_x, T u_y, C u_x, C u_y) at the previous collision. */

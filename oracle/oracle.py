@@ -42,7 +42,8 @@ class Params(C.Structure):
         ("s", C.c_double * 9), ("zeta", C.c_double * 5), ("eta", C.c_double * 5),
         ("periodic_x", C.c_int), ("periodic_y", C.c_int),
         ("scalar_lr", C.c_int), ("scalar_tb", C.c_int),
-        ("Tw", C.c_double * 2), ("Cw", C.c_double * 2),
+        ("Tw", C.c_double * 4), ("Cw", C.c_double * 4),
+        ("uw", (C.c_double * 2) * 4),
         ("Gx", C.c_double),
         ("model_a", C.c_int),
     ]
@@ -78,6 +79,7 @@ def lib():
             L.or_time.restype = C.c_long
             L.or_fields.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
             L.or_nusselt_sherwood.argtypes = [C.c_void_p, dp]
+            L.or_nusselt_sherwood_tb.argtypes = [C.c_void_p, dp]
             L.or_get.argtypes = [C.c_void_p, dp, dp, dp, dp]
             L.or_set.argtypes = [C.c_void_p, dp, dp, dp, dp]
             L.or_collide_node.argtypes = [P, dp, dp, dp, dp, dp, dp, dp, dp]
@@ -105,6 +107,28 @@ def derive(nx, ny, Ra, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, Ma=0.1, varpi=0.4) 
     rc = lib().or_derive(C.byref(p))
     if rc != 0:
         raise ValueError(f"invalid parameters (or_derive returned {rc})")
+    return p
+
+
+def derive_lid(nx, ny, Re, Gr, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, U0=0.1, varpi=0.4) -> Params:
+    """Lid-driven porous cavity of Sec. 4.3: the top wall moves with U0 along +x, top
+    T = C = 1, bottom T = C = 0, left/right adiabatic; Re = L U0 / nu with
+    1/s_nu = 1/2 + J L U0 / (c_s^2 Re); Gr = g beta_T dT L^3 / nu^2 (L = nx)."""
+    p = derive(nx, ny, 1e4, Da, eps, Pr, Le, N, J, sigma, 0.1, varpi)
+    L = float(nx)
+    nu_e = J * L * U0 / Re
+    p.nu_e, p.nu = nu_e, nu_e / J
+    p.alpha_e = p.nu / Pr
+    p.D_e = p.alpha_e / Le
+    p.s[7] = p.s[8] = 1.0 / (0.5 + nu_e / p.cs2)
+    p.zeta[1] = p.zeta[2] = 1.0 / (0.5 + p.alpha_e / p.csT2)
+    p.eta[1] = p.eta[2] = 1.0 / (0.5 + p.D_e / p.csT2)
+    p.gbT = Gr * p.nu * p.nu / L ** 3
+    p.gbC = N * p.gbT
+    p.scalar_lr, p.scalar_tb = ADIABATIC, DIRICHLET
+    for k, v in enumerate((0.5, 0.5, 0.0, 1.0)):
+        p.Tw[k] = p.Cw[k] = v
+    p.uw[3][0] = U0
     return p
 
 
@@ -168,6 +192,11 @@ class Oracle:
     def nusselt_sherwood(self) -> np.ndarray:
         out = np.empty(4)
         lib().or_nusselt_sherwood(self.h, _ptr(out))
+        return out
+
+    def nusselt_sherwood_tb(self) -> np.ndarray:
+        out = np.empty(4)
+        lib().or_nusselt_sherwood_tb(self.h, _ptr(out))
         return out
 
     def get(self):

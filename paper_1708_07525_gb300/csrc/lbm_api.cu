@@ -81,6 +81,12 @@ Coef<R> make_coef(const lbm_params& P) {
     c.dirichlet_mask = (P.wall_lr == LBM_WALL_DIRICHLET ? 3 : 0) |
                        (P.wall_tb == LBM_WALL_DIRICHLET ? 12 : 0);
     c.sr = 1;
+    c.moving = 0;
+    for (int s = 0; s < 4; ++s)
+        for (int d = 0; d < 2; ++d) {
+            c.wmom[s][d] = (R)(2.0 * 1.0 * P.uw[s][d] / (1.0 / 3.0));   // 2 rho0 u_w / c_s^2
+            if (P.uw[s][d] != 0.0) c.moving = 1;
+        }
     return c;
 }
 template Coef<float> make_coef<float>(const lbm_params&);
@@ -358,6 +364,47 @@ lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, do
     const char* bad = check_params(P);
     if (bad) {
         set_global_error("lbm_derive_params: %s (s_nu=%g zeta_a=%g eta_D=%g)", bad, s_nu, za, eD);
+        return LBM_ERR_INVALID;
+    }
+    *out = P;
+    return LBM_OK;
+}
+
+lbm_status lbm_derive_params_lid(lbm_grid grid, double Re, double Gr, double Da, double eps,
+                                 double Pr, double Le, double N, double J, double sigma,
+                                 double U0, double varpi, lbm_params* out) {
+    if (!out || grid.nx < 3 || grid.ny < 3 || !(Re > 0.0) || !(Gr >= 0.0) || !(Da > 0.0) ||
+        !(eps > 0.0 && eps <= 1.0) || !(Pr > 0.0) || !(Le > 0.0) || !(J > 0.0) || !(sigma > 0.0)) {
+        set_global_error("lbm_derive_params_lid: invalid arguments");
+        return LBM_ERR_INVALID;
+    }
+    if (!(U0 > 0.0)) U0 = 0.1;
+    if (!(varpi > 0.0)) varpi = 0.4;
+    // reuse the cavity mapping for everything but the flow scales, then set those (Sec. 4.3)
+    lbm_status st = lbm_derive_params(grid, 1e4, Da, eps, Pr, Le, N, J, sigma, 0.1, varpi, out);
+    if (st != LBM_OK) return st;
+    lbm_params P = *out;
+    const double L = grid.nx, cs2 = 1.0 / 3.0, csT2 = 0.5 * varpi;
+    const double nu_e = J * L * U0 / Re;             // 1/s_nu = 1/2 + J L U0 / (c_s^2 Re)
+    const double nu = nu_e / J;
+    const double alpha_e = nu / Pr, D_e = alpha_e / Le;
+    const double s_nu = 1.0 / (0.5 + nu_e / cs2);
+    P.nu = nu;
+    P.s[7] = P.s[8] = s_nu;
+    P.zeta[1] = P.zeta[2] = 1.0 / (0.5 + alpha_e / csT2);   // Eq. 29
+    P.eta[1] = P.eta[2] = 1.0 / (0.5 + D_e / csT2);
+    P.gbT = Gr * nu * nu / (L * L * L);                       // Gr = g beta_T dT L^3 / nu^2
+    P.gbC = N * P.gbT;
+    const double Tw[4] = {0.5, 0.5, 0.0, 1.0};               // bottom cold, top hot
+    std::memcpy(P.Tw, Tw, sizeof Tw);
+    std::memcpy(P.Cw, Tw, sizeof Tw);
+    P.wall_lr = LBM_WALL_ADIABATIC;
+    P.wall_tb = LBM_WALL_DIRICHLET;
+    std::memset(P.uw, 0, sizeof P.uw);
+    P.uw[3][0] = U0;                                          // the lid
+    const char* bad = check_params(P);
+    if (bad) {
+        set_global_error("lbm_derive_params_lid: %s", bad);
         return LBM_ERR_INVALID;
     }
     *out = P;
@@ -654,6 +701,38 @@ lbm_status lbm_nusselt_sherwood(lbm_ctx* c, double out[4]) {
         if (!std::isfinite(out[k]))
             return c->fail(LBM_ERR_DIVERGED, "lbm_nusselt_sherwood: non-finite result at t=%lld",
                            (long long)c->t);
+    return LBM_OK;
+}
+
+lbm_status lbm_nusselt_sherwood_tb(lbm_ctx* c, double out[4]) {
+    if (!c || !out) {
+        set_global_error("lbm_nusselt_sherwood_tb: NULL argument");
+        return LBM_ERR_INVALID;
+    }
+    DeviceGuard dg(c->device);
+    WallSpec W;
+    W.Tw[0] = c->P.Tw[2];
+    W.Tw[1] = c->P.Tw[3];
+    W.Cw[0] = c->P.Cw[2];
+    W.Cw[1] = c->P.Cw[3];
+    W.T0 = c->P.T0;
+    W.C0 = c->P.C0;
+    W.dT = c->P.Tw[3] - c->P.Tw[2];
+    W.dC = c->P.Cw[3] - c->P.Cw[2];
+    W.L = c->P.ny;
+    const int mode = c->read_mode();
+    const void* b = cur_buf(c);
+    cudaError_t e = LBM_DISPATCH(c, launch_nush_tb<double>(b, c->G, c->cd, mode, W, c->d_out + 20, c->stream),
+                                 launch_nush_tb<float>(b, c->G, c->cf, mode, W, c->d_out + 20, c->stream),
+                                 launch_nush_tb<__nv_bfloat16>(b, c->G, c->cf, mode, W, c->d_out + 20, c->stream),
+                                 launch_nush_tb<__half>(b, c->G, c->cf, mode, W, c->d_out + 20, c->stream));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, c->d_out + 20, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "lbm_nusselt_sherwood_tb");
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(out[k]))
+            return c->fail(LBM_ERR_DIVERGED, "lbm_nusselt_sherwood_tb: non-finite result");
     return LBM_OK;
 }
 

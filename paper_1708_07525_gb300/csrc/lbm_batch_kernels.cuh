@@ -71,14 +71,7 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
                 load_hist(hist, G, self, hv);
                 uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
                 collide(I.c, f, g, h, hv);
-#pragma unroll
-                for (int q = 0; q < 9; ++q)
-                    put(dst + (size_t)(QF + q) * G.plane + self, f[q], I.c.sr, seed, q);
-#pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    put(dst + (size_t)(QG + q) * G.plane + self, g[q], I.c.sr, seed, QG + q);
-                    put(dst + (size_t)(QH + q) * G.plane + self, h[q], I.c.sr, seed, QH + q);
-                }
+                store_ab(dst, G, self, I.c, f, g, h, seed);
             } else {
                 S* buf = (S*)I.buf[0];
                 if (odd)
@@ -88,44 +81,10 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
                 load_hist(hist, G, self, hv);
                 uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
                 collide(I.c, f, g, h, hv);
-                if (!odd) {
-#pragma unroll
-                    for (int q = 0; q < 9; ++q)
-                        put(buf + (size_t)(QF + opp_of(q)) * G.plane + self, f[q], I.c.sr, seed, q);
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) {
-                        put(buf + (size_t)(QG + opp_of(q)) * G.plane + self, g[q], I.c.sr, seed,
-                            QG + q);
-                        put(buf + (size_t)(QH + opp_of(q)) * G.plane + self, h[q], I.c.sr, seed,
-                            QH + q);
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 9; ++q) {
-                        const int ti = i + ex_of(q), tj = j + ey_of(q);
-                        const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
-                        S* p = in ? buf + (size_t)(QF + q) * G.plane + (size_t)tj * G.pitch + ti
-                                  : buf + (size_t)(QF + opp_of(q)) * G.plane + self;
-                        put(p, f[q], I.c.sr, seed, q);
-                    }
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) {
-                        const int ti = i + ex_of(q), tj = j + ey_of(q);
-                        const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
-                        R vg = g[q], vh = h[q];
-                        size_t off = self;
-                        int slot = opp_of(q);
-                        if (in) {
-                            off = (size_t)tj * G.pitch + ti;
-                            slot = q;
-                        } else if (q > 0) {
-                            vg = wall_value(I.c, I.c.wallT, push_side(q), vg);
-                            vh = wall_value(I.c, I.c.wallC, push_side(q), vh);
-                        }
-                        put(buf + (size_t)(QG + slot) * G.plane + off, vg, I.c.sr, seed, QG + q);
-                        put(buf + (size_t)(QH + slot) * G.plane + off, vh, I.c.sr, seed, QH + q);
-                    }
-                }
+                if (odd)
+                    store_aa_odd(buf, G, i, j, self, I.c, f, g, h, seed);
+                else
+                    store_aa_even(buf, G, self, I.c, f, g, h, seed);
             }
             store_hist(hist, G, self, hv);
         }
@@ -163,14 +122,7 @@ batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
         load_hist(hist, G, self, hv);
         uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
         collide(I.c, f, g, h, hv);
-#pragma unroll
-        for (int q = 0; q < 9; ++q)
-            put(dst + (size_t)(QF + q) * G.plane + self, f[q], I.c.sr, seed, q);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            put(dst + (size_t)(QG + q) * G.plane + self, g[q], I.c.sr, seed, QG + q);
-            put(dst + (size_t)(QH + q) * G.plane + self, h[q], I.c.sr, seed, QH + q);
-        }
+        store_ab(dst, G, self, I.c, f, g, h, seed);
     } else {
         S* buf = (S*)I.buf[0];
         if (odd)
@@ -180,42 +132,10 @@ batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
         load_hist(hist, G, self, hv);
         uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
         collide(I.c, f, g, h, hv);
-        if (!odd) {
-#pragma unroll
-            for (int q = 0; q < 9; ++q)
-                put(buf + (size_t)(QF + opp_of(q)) * G.plane + self, f[q], I.c.sr, seed, q);
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                put(buf + (size_t)(QG + opp_of(q)) * G.plane + self, g[q], I.c.sr, seed, QG + q);
-                put(buf + (size_t)(QH + opp_of(q)) * G.plane + self, h[q], I.c.sr, seed, QH + q);
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                const int ti = i + ex_of(q), tj = j + ey_of(q);
-                const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
-                S* p = in ? buf + (size_t)(QF + q) * G.plane + (size_t)tj * G.pitch + ti
-                          : buf + (size_t)(QF + opp_of(q)) * G.plane + self;
-                put(p, f[q], I.c.sr, seed, q);
-            }
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                const int ti = i + ex_of(q), tj = j + ey_of(q);
-                const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
-                R vg = g[q], vh = h[q];
-                size_t off = self;
-                int slot = opp_of(q);
-                if (in) {
-                    off = (size_t)tj * G.pitch + ti;
-                    slot = q;
-                } else if (q > 0) {
-                    vg = wall_value(I.c, I.c.wallT, push_side(q), vg);
-                    vh = wall_value(I.c, I.c.wallC, push_side(q), vh);
-                }
-                put(buf + (size_t)(QG + slot) * G.plane + off, vg, I.c.sr, seed, QG + q);
-                put(buf + (size_t)(QH + slot) * G.plane + off, vh, I.c.sr, seed, QH + q);
-            }
-        }
+        if (odd)
+            store_aa_odd(buf, G, i, j, self, I.c, f, g, h, seed);
+        else
+            store_aa_even(buf, G, self, I.c, f, g, h, seed);
     }
     store_hist(hist, G, self, hv);
 }

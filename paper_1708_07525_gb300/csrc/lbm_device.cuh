@@ -30,6 +30,11 @@ __host__ __device__ constexpr int opp_of(int q) {
 static_assert(opp_of(1) == 3 && opp_of(3) == 1 && opp_of(2) == 4 && opp_of(4) == 2, "opp");
 static_assert(opp_of(5) == 7 && opp_of(7) == 5 && opp_of(6) == 8 && opp_of(8) == 6, "opp");
 
+// D2Q9 weights (Eq. 20).
+__host__ __device__ constexpr double w9_of(int q) {
+    return q == 0 ? 4.0 / 9.0 : (q <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
 // Plane index of each lattice inside the 19-plane state: f 0..8, g 9..13, h 14..18.
 constexpr int QF = 0, QG = 9, QH = 14, NQ = 19;
 
@@ -139,6 +144,9 @@ struct Coef {
     R wallT[4], wallC[4];
     int dirichlet_mask;        // bit s set: side s is Dirichlet for g and h, else adiabatic
     int sr;                    // 1: stochastic rounding when storing 16-bit populations
+    // Moving walls: wmom[s] = 2 rho0 u_w / c_s^2 of side s; moving = 1 if any is nonzero.
+    R wmom[4][2];
+    int moving;
 };
 
 template <typename R> __device__ __forceinline__ R sqrt_(R x);

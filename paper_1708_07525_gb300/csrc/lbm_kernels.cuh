@@ -24,6 +24,20 @@ __device__ __forceinline__ R wall_value(const Coef<R>& c, const R* wall, int sid
     return ((c.dirichlet_mask >> side) & 1) ? wall[side] - reflected : reflected;
 }
 
+// Wall side of a link whose far end (ti, tj) lies outside the cavity; a link
+// through a corner takes the bottom / top wall.
+__device__ __forceinline__ int link_side(int ti, int tj, const Geom& G) {
+    return (unsigned)tj >= (unsigned)G.ny ? (tj < 0 ? 2 : 3) : (ti < 0 ? 0 : 1);
+}
+
+// Momentum a wall moving with u_w gives a population bounced back into direction q:
+// 2 w_q rho0 (e_q . u_w) / c_s^2 (halfway bounce-back off a moving wall; the
+// no-slip rule is u_w = 0).
+template <typename R>
+__device__ __forceinline__ R wall_momentum(const Coef<R>& c, int side, int q) {
+    return R(w9_of(q)) * (R(ex_of(q)) * c.wmom[side][0] + R(ey_of(q)) * c.wmom[side][1]);
+}
+
 // Pre-collision populations of node (i, j) at level t from a buffer of level
 // t-1 post-collision values (pull streaming, Eq. 11, with the halfway wall
 // rules).  SWAP = false: two-buffer layout, slot q of the source node.
@@ -41,7 +55,8 @@ __device__ __forceinline__ void gather_pull(const S* __restrict__ buf, const Geo
             const int slot_self = SWAP ? q : opp_of(q);
             const S* p = in ? buf + (size_t)(QF + slot_src) * G.plane + (size_t)sj * G.pitch + si
                             : buf + (size_t)(QF + slot_self) * G.plane + self;
-            f[q] = Store<S>::ld(p);   // no-slip halfway bounce-back when !in
+            f[q] = Store<S>::ld(p);   // halfway bounce-back when !in
+            if (!in && c.moving) f[q] += wall_momentum(c, link_side(si, sj, G), q);
         }
     }
 #pragma unroll
@@ -103,6 +118,71 @@ __device__ __forceinline__ void store_hist(R* __restrict__ hist, const Geom& G, 
     for (int k = 0; k < 4; ++k) hist[(size_t)k * G.plane + self] = hv[k];
 }
 
+// ---- stores of a node's post-collision populations ----------------------------------
+// Two-buffer layout: slot q of the node itself in the destination buffer.
+template <typename S, typename R>
+__device__ __forceinline__ void store_ab(S* __restrict__ dst, const Geom& G, size_t self,
+                                         const Coef<R>& c, const R f[9], const R g[5],
+                                         const R h[5], uint32_t& seed) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) put(dst + (size_t)(QF + q) * G.plane + self, f[q], c.sr, seed, q);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        put(dst + (size_t)(QG + q) * G.plane + self, g[q], c.sr, seed, QG + q);
+        put(dst + (size_t)(QH + q) * G.plane + self, h[q], c.sr, seed, QH + q);
+    }
+}
+
+// In-place layout, even step: slot opp(q) of the node itself.
+template <typename S, typename R>
+__device__ __forceinline__ void store_aa_even(S* __restrict__ buf, const Geom& G, size_t self,
+                                              const Coef<R>& c, const R f[9], const R g[5],
+                                              const R h[5], uint32_t& seed) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+        put(buf + (size_t)(QF + opp_of(q)) * G.plane + self, f[q], c.sr, seed, q);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        put(buf + (size_t)(QG + opp_of(q)) * G.plane + self, g[q], c.sr, seed, QG + q);
+        put(buf + (size_t)(QH + opp_of(q)) * G.plane + self, h[q], c.sr, seed, QH + q);
+    }
+}
+
+// In-place layout, odd step: slot q of the neighbour x + e_q, or, where that link
+// crosses a wall, the wall rule's value in slot opp(q) of the node itself.
+template <typename S, typename R>
+__device__ __forceinline__ void store_aa_odd(S* __restrict__ buf, const Geom& G, int i, int j,
+                                             size_t self, const Coef<R>& c, const R f[9],
+                                             const R g[5], const R h[5], uint32_t& seed) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int ti = i + ex_of(q), tj = j + ey_of(q);
+        const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
+        S* p = in ? buf + (size_t)(QF + q) * G.plane + (size_t)tj * G.pitch + ti
+                  : buf + (size_t)(QF + opp_of(q)) * G.plane + self;
+        R v = f[q];
+        if (!in && c.moving) v -= wall_momentum(c, link_side(ti, tj, G), q);
+        put(p, v, c.sr, seed, q);
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int ti = i + ex_of(q), tj = j + ey_of(q);
+        const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
+        R vg = g[q], vh = h[q];
+        size_t off = self;
+        int slot = opp_of(q);
+        if (in) {
+            off = (size_t)tj * G.pitch + ti;
+            slot = q;
+        } else if (q > 0) {
+            vg = wall_value(c, c.wallT, push_side(q), vg);
+            vh = wall_value(c, c.wallC, push_side(q), vh);
+        }
+        put(buf + (size_t)(QG + slot) * G.plane + off, vg, c.sr, seed, QG + q);
+        put(buf + (size_t)(QH + slot) * G.plane + off, vh, c.sr, seed, QH + q);
+    }
+}
+
 // ---- the fused step, two-buffer pull layout ---------------------------------------
 template <typename S>
 __global__ void __launch_bounds__(256)
@@ -119,13 +199,7 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
     load_hist(hist, G, self, hv);
     uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
     collide(c, f, g, h, hv);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) put(dst + (size_t)(QF + q) * G.plane + self, f[q], c.sr, seed, q);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        put(dst + (size_t)(QG + q) * G.plane + self, g[q], c.sr, seed, QG + q);
-        put(dst + (size_t)(QH + q) * G.plane + self, h[q], c.sr, seed, QH + q);
-    }
+    store_ab(dst, G, self, c, f, g, h, seed);
     store_hist(hist, G, self, hv);
 }
 
@@ -154,42 +228,10 @@ step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, G
     load_hist(hist, G, self, hv);
     uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
     collide(c, f, g, h, hv);
-    if (!ODD) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q)
-            put(buf + (size_t)(QF + opp_of(q)) * G.plane + self, f[q], c.sr, seed, q);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            put(buf + (size_t)(QG + opp_of(q)) * G.plane + self, g[q], c.sr, seed, QG + q);
-            put(buf + (size_t)(QH + opp_of(q)) * G.plane + self, h[q], c.sr, seed, QH + q);
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const int ti = i + ex_of(q), tj = j + ey_of(q);
-            const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
-            S* p = in ? buf + (size_t)(QF + q) * G.plane + (size_t)tj * G.pitch + ti
-                      : buf + (size_t)(QF + opp_of(q)) * G.plane + self;
-            put(p, f[q], c.sr, seed, q);
-        }
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const int ti = i + ex_of(q), tj = j + ey_of(q);
-            const bool in = (unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny;
-            R vg = g[q], vh = h[q];
-            size_t off = self;
-            int slot = opp_of(q);
-            if (in) {
-                off = (size_t)tj * G.pitch + ti;
-                slot = q;
-            } else if (q > 0) {
-                vg = wall_value(c, c.wallT, push_side(q), vg);
-                vh = wall_value(c, c.wallC, push_side(q), vh);
-            }
-            put(buf + (size_t)(QG + slot) * G.plane + off, vg, c.sr, seed, QG + q);
-            put(buf + (size_t)(QH + slot) * G.plane + off, vh, c.sr, seed, QH + q);
-        }
-    }
+    if (ODD)
+        store_aa_odd(buf, G, i, j, self, c, f, g, h, seed);
+    else
+        store_aa_even(buf, G, self, c, f, g, h, seed);
     store_hist(hist, G, self, hv);
 }
 
@@ -231,8 +273,16 @@ __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restr
     const size_t self = (size_t)j * G.pitch + i;
     double Tp, Cp;
     initial_TC(I, G, i, j, Tp, Cp);
+    // flow at rest: f' = 0; in the pull layout a slot whose link leaves the cavity holds
+    // the value the moving-wall rule turns into 0 (wall_momentum of that wall).
 #pragma unroll
-    for (int q = 0; q < 9; ++q) Store<S>::st(buf + (size_t)(QF + q) * G.plane + self, R(0));
+    for (int q = 0; q < 9; ++q) {
+        R v = R(0);
+        const int ti = i + ex_of(q), tj = j + ey_of(q);
+        if (PULL && c.moving && !((unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny))
+            v = wall_momentum(c, link_side(ti, tj, G), q);
+        Store<S>::st(buf + (size_t)(QF + q) * G.plane + self, v);
+    }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         double vg, vh;
@@ -349,6 +399,47 @@ nush_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c, i
         double s = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
         out[threadIdx.x] = s / G.ny;
+    }
+}
+
+// Mean Nu / Sh on the bottom and top walls, one block, FP64, fixed reduction order.
+// W.Tw / W.Cw = {bottom, top}; out = {Nu_B, Sh_B, Nu_T, Sh_T}.
+template <typename S>
+__global__ void __launch_bounds__(NUSH_THREADS)
+nush_tb_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c, int mode,
+               WallSpec W, double* __restrict__ out) {
+    using R = typename Real<S>::type;
+    double acc[4] = {0, 0, 0, 0};
+    for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
+        R f[9], g[5], h[5];
+        double T[4], C[4];
+        const int rows[4] = {0, 1, G.ny - 2, G.ny - 1};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            gather<false>(mode, buf, G, i, rows[k], c, f, g, h);
+            const R sg = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+            const R sh = ((h[0] + h[1]) + (h[2] + h[3])) + h[4];
+            T[k] = W.T0 + (double)(sg * c.inv_sigma);
+            C[k] = W.C0 + (double)(sh * c.inv_eps);
+        }
+        // dPhi/dy at the wall through the wall value and the first two rows
+        acc[0] += W.L * (-8.0 * W.Tw[0] + 9.0 * T[0] - T[1]) / 3.0 / W.dT;
+        acc[1] += W.L * (-8.0 * W.Cw[0] + 9.0 * C[0] - C[1]) / 3.0 / W.dC;
+        acc[2] += W.L * (8.0 * W.Tw[1] - 9.0 * T[3] + T[2]) / 3.0 / W.dT;
+        acc[3] += W.L * (8.0 * W.Cw[1] - 9.0 * C[3] + C[2]) / 3.0 / W.dC;
+    }
+    __shared__ double red[NUSH_THREADS / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s / G.nx;
     }
 }
 

@@ -59,6 +59,10 @@ cudaError_t launch_fields(const void* buf, const Geom& G, const Coef<typename Re
 template <typename S>
 cudaError_t launch_nush(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
                         int mode, const WallSpec& W, double* out, cudaStream_t st);
+// Nu / Sh on the bottom (Tw[0], Cw[0]) and top (Tw[1], Cw[1]) walls; out 4 doubles.
+template <typename S>
+cudaError_t launch_nush_tb(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
+                           int mode, const WallSpec& W, double* out, cudaStream_t st);
 // partial must hold residual_blocks(G) * 9 doubles; out 9 doubles.
 template <typename S>
 cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,

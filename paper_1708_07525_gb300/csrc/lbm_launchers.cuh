@@ -59,6 +59,13 @@ cudaError_t launch_nush(const void* buf, const Geom& G, const Coef<typename Real
 }
 
 template <typename S>
+cudaError_t launch_nush_tb(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
+                           int mode, const WallSpec& W, double* out, cudaStream_t st) {
+    nush_tb_kernel<S><<<1, NUSH_THREADS, 0, st>>>((const S*)buf, G, c, mode, W, out);
+    return cudaGetLastError();
+}
+
+template <typename S>
 cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
                             int mode, double* snap, double* partial, double* out,
                             cudaStream_t st) {
@@ -84,6 +91,8 @@ cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename 
                                           double*, cudaStream_t);                              \
     template cudaError_t launch_nush<S>(const void*, const Geom&, const Coef<Real<S>::type>&,  \
                                         int, const WallSpec&, double*, cudaStream_t);          \
+    template cudaError_t launch_nush_tb<S>(const void*, const Geom&, const Coef<Real<S>::type>&,\
+                                           int, const WallSpec&, double*, cudaStream_t);       \
     template cudaError_t launch_residual<S>(const void*, const Geom&,                          \
                                             const Coef<Real<S>::type>&, int, double*, double*, \
                                             double*, cudaStream_t);

@@ -59,7 +59,8 @@ class lbm_params(C.Structure):
         ("gbT", C.c_double), ("gbC", C.c_double), ("Gx", C.c_double), ("T0", C.c_double),
         ("C0", C.c_double), ("s", C.c_double * 9), ("zeta", C.c_double * 5),
         ("eta", C.c_double * 5), ("Tw", C.c_double * 4), ("Cw", C.c_double * 4),
-        ("wall_lr", C.c_int), ("wall_tb", C.c_int), ("model_a", C.c_int),
+        ("wall_lr", C.c_int), ("wall_tb", C.c_int), ("uw", (C.c_double * 2) * 4),
+        ("model_a", C.c_int),
     ]
 
 
@@ -84,6 +85,8 @@ def lib():
             L.lbm_create_raw.argtypes = [C.POINTER(lbm_params), C.POINTER(lbm_options),
                                          C.POINTER(C.c_void_p)]
             L.lbm_params_model_a.argtypes = [C.POINTER(lbm_params)]
+            L.lbm_derive_params_lid.argtypes = [lbm_grid] + [C.c_double] * 11 + [C.POINTER(lbm_params)]
+            L.lbm_nusselt_sherwood_tb.argtypes = [P, dp]
             L.lbm_reset.argtypes = [P, dp, dp, C.c_uint64, C.c_double]
             L.lbm_step.argtypes = [P, C.c_int64]
             L.lbm_time.argtypes = [P]
@@ -101,7 +104,8 @@ def lib():
             L.lbm_destroy.argtypes = [P]
             L.lbm_last_error.argtypes = [P]
             L.lbm_last_error.restype = C.c_char_p
-            for name in ("lbm_derive_params", "lbm_params_model_a", "lbm_create", "lbm_create_raw",
+            for name in ("lbm_derive_params", "lbm_params_model_a", "lbm_derive_params_lid",
+                         "lbm_nusselt_sherwood_tb", "lbm_create", "lbm_create_raw",
                          "lbm_reset", "lbm_step",
                          "lbm_fields", "lbm_fields_window", "lbm_nusselt_sherwood", "lbm_residual",
                          "lbm_residual_noalloc", "lbm_save",
@@ -156,6 +160,14 @@ def lbm_derive_params(nx, ny, Ra, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, Ma=0.0, 
     p = lbm_params()
     _check(lib().lbm_derive_params(lbm_grid(int(nx), int(ny)), Ra, Da, eps, Pr, Le, N, J, sigma,
                                    Ma, varpi, C.byref(p)))
+    return p
+
+
+def lbm_derive_params_lid(nx, ny, Re, Gr, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, U0=0.1,
+                          varpi=0.0):
+    p = lbm_params()
+    _check(lib().lbm_derive_params_lid(lbm_grid(int(nx), int(ny)), Re, Gr, Da, eps, Pr, Le, N, J,
+                                       sigma, U0, varpi, C.byref(p)))
     return p
 
 
@@ -257,6 +269,11 @@ class Cavity:
     def nusselt_sherwood(self):
         out = np.empty(4)
         _check(lib().lbm_nusselt_sherwood(self.h, _dptr(out)), self.h)
+        return out
+
+    def nusselt_sherwood_tb(self):
+        out = np.empty(4)
+        _check(lib().lbm_nusselt_sherwood_tb(self.h, _dptr(out)), self.h)
         return out
 
     def residual(self):

@@ -192,7 +192,9 @@ def test_precision_study_cavity_fp64_against_oracle(oracle_mod):
     gpu, ora = make_pair(oracle_mod, PRECISION_STUDY, "f64", "ab")
     gpu.step(200)
     ora.step(200)
-    compare(gpu, ora, 1e-12, nush_tol=1e-12)
+    # after 200 steps most of this large cavity is still at rest: u ~ 1e-6 there, below the
+    # unshifted oracle's own rounding on sums of O(0.1) populations
+    compare(gpu, ora, 1e-12, nush_tol=1e-12, u_atol=1e-15)
 
 
 @pytest.mark.parametrize("layout", ["ab", "aa"])
