@@ -90,6 +90,11 @@ typedef struct {
     void* alloc_user;
     int block_x, block_y;       /* launch tile of the step kernel; 0 -> tuned default */
     int graph_chunk;            /* steps per captured CUDA graph; 0 -> default, <0 -> off */
+    const double* eps_field;    /* optional host [ny][nx] porosity field: the REV model with
+                                   spatially varying eps (Sec. 2-3 applied per node, F_eps of
+                                   Eq. 7 per node); values in (0, 1]; NULL -> uniform eps */
+    const double* K_field;      /* optional host [ny][nx] permeability field (> 0); NULL ->
+                                   uniform K.  Not with model_a.  Copied at create. */
     int round_nearest;          /* 16-bit storage: 0 (default) -> stochastic rounding of every
                                    stored population (unbiased; random bits hashed from the
                                    node index and its pre-collision state, so runs are

@@ -152,7 +152,20 @@ struct or_state {
     size_t n;
     double *f, *g, *h, *hist;   /* pre-collision distributions at time t */
     double *f2, *g2, *h2;       /* streaming targets */
+    double *eps, *K;            /* optional per-node porosity / permeability */
 };
+
+/* The parameters at node x: the uniform ones, or with that node's eps, K, F_eps. */
+static or_params node_params(const or_state* s, size_t x)
+{
+    or_params q = s->p;
+    if (s->eps) {
+        q.eps = s->eps[x];
+        q.Feps = 1.75 / sqrt(150.0 * q.eps * q.eps * q.eps);   /* Eq. 7 */
+    }
+    if (s->K) q.K = s->K[x];
+    return q;
+}
 
 long or_time(const or_state* s) { return s->t; }
 
@@ -315,6 +328,12 @@ void or_collide_node(const or_params* p, const double f[9], const double g[5],
 or_state* or_create(const or_params* p, uint64_t seed, double noise, const double* T_init,
                     const double* C_init)
 {
+    return or_create_field(p, seed, noise, T_init, C_init, NULL, NULL);
+}
+
+or_state* or_create_field(const or_params* p, uint64_t seed, double noise, const double* T_init,
+                          const double* C_init, const double* eps_field, const double* K_field)
+{
     ensure_inverses();
     or_state* s = (or_state*)calloc(1, sizeof(or_state));
     if (!s) return NULL;
@@ -332,10 +351,21 @@ or_state* or_create(const or_params* p, uint64_t seed, double noise, const doubl
         or_destroy(s);
         return NULL;
     }
+    if (eps_field) {
+        s->eps = (double*)malloc(n * sizeof(double));
+        if (!s->eps) { or_destroy(s); return NULL; }
+        memcpy(s->eps, eps_field, n * sizeof(double));
+    }
+    if (K_field) {
+        s->K = (double*)malloc(n * sizeof(double));
+        if (!s->K) { or_destroy(s); return NULL; }
+        memcpy(s->K, K_field, n * sizeof(double));
+    }
     double varpi = p->varpi;
     for (int j = 0; j < p->ny; ++j)
         for (int i = 0; i < p->nx; ++i) {
             size_t x = (size_t)j * p->nx + i;
+            const double eps_x = s->eps ? s->eps[x] : p->eps;
             /* noise key: (field * ny + j) * nx + i, field 0 = T, 1 = C */
             double T = T_init ? T_init[x]
                               : p->T0 + noise * (2.0 * or_uniform(seed, x) - 1.0);
@@ -346,17 +376,17 @@ or_state* or_create(const or_params* p, uint64_t seed, double noise, const doubl
             /* Eq. 28 at u = 0; model A: g_i^eq = w~_i T (sigma + e_i.u / c_sT^2) at u = 0 */
             if (!p->model_a) {
                 s->g[x] = p->sigma * T - varpi * T;
-                s->h[x] = p->eps * C - varpi * C;
+                s->h[x] = eps_x * C - varpi * C;
                 for (int q = 1; q < 5; ++q) {
                     s->g[q * n + x] = varpi / 4 * T;
                     s->h[q * n + x] = varpi / 4 * C;
                 }
             } else {
                 s->g[x] = (1.0 - varpi) * p->sigma * T;
-                s->h[x] = (1.0 - varpi) * p->eps * C;
+                s->h[x] = (1.0 - varpi) * eps_x * C;
                 for (int q = 1; q < 5; ++q) {
                     s->g[q * n + x] = varpi / 4 * p->sigma * T;
-                    s->h[q * n + x] = varpi / 4 * p->eps * C;
+                    s->h[q * n + x] = varpi / 4 * eps_x * C;
                 }
             }
         }
@@ -366,7 +396,8 @@ or_state* or_create(const or_params* p, uint64_t seed, double noise, const doubl
         for (int q = 0; q < 9; ++q) fl[q] = s->f[q * n + x];
         for (int q = 0; q < 5; ++q) { gl[q] = s->g[q * n + x]; hl[q] = s->h[q * n + x]; }
         or_macro o;
-        macro(&s->p, fl, gl, hl, &o);
+        or_params px = node_params(s, x);
+        macro(&px, fl, gl, hl, &o);
         s->hist[0 * n + x] = o.T * o.ux;
         s->hist[1 * n + x] = o.T * o.uy;
         s->hist[2 * n + x] = o.C * o.ux;
@@ -380,6 +411,7 @@ void or_destroy(or_state* s)
     if (!s) return;
     free(s->f); free(s->g); free(s->h); free(s->hist);
     free(s->f2); free(s->g2); free(s->h2);
+    free(s->eps); free(s->K);
     free(s);
 }
 
@@ -403,7 +435,8 @@ void or_step(or_state* s, long nsteps)
                 for (int q = 0; q < 5; ++q) { g[q] = s->g[q * n + x]; h[q] = s->h[q * n + x]; }
                 for (int k = 0; k < 4; ++k) hist[k] = s->hist[k * n + x];
                 or_macro o;
-                collide(p, f, g, h, hist, fs, gs, hs, &o);
+                const or_params px = node_params(s, x);
+                collide(&px, f, g, h, hist, fs, gs, hs, &o);
                 for (int k = 0; k < 4; ++k) s->hist[k * n + x] = hist[k];
                 /* Eq. 11: push f*_q to x + e_q; links that leave the cavity are
                  * reflected at the halfway wall back into the opposite slot of x. */
@@ -437,7 +470,7 @@ void or_step(or_state* s, long nsteps)
                         /* anti-bounce-back: g_opp(x) = -g*_q(x) + g_q^eq(T_w) + g_opp^eq(T_w),
                          * = 2 w~ T_w (Eq. 28), = 2 w~ sigma T_w (model A) */
                         int side = lr ? (ti < 0 ? 0 : 1) : (tj < 0 ? 2 : 3);
-                        double kg = p->model_a ? p->sigma : 1.0, kh = p->model_a ? p->eps : 1.0;
+                        double kg = p->model_a ? p->sigma : 1.0, kh = p->model_a ? px.eps : 1.0;
                         s->g2[opp[q] * n + x] = -gs[q] + 2.0 * wt_axis * kg * p->Tw[side];
                         s->h2[opp[q] * n + x] = -hs[q] + 2.0 * wt_axis * kh * p->Cw[side];
                     } else {
@@ -466,7 +499,8 @@ void or_fields(const or_state* s, double* ux, double* uy, double* T, double* C, 
         for (int q = 0; q < 9; ++q) f[q] = s->f[q * n + x];
         for (int q = 0; q < 5; ++q) { g[q] = s->g[q * n + x]; h[q] = s->h[q * n + x]; }
         or_macro o;
-        macro(&s->p, f, g, h, &o);
+        const or_params px = node_params(s, x);
+        macro(&px, f, g, h, &o);
         if (ux) ux[x] = o.ux;
         if (uy) uy[x] = o.uy;
         if (T) T[x] = o.T;

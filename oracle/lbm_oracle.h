@@ -76,6 +76,12 @@ int or_derive(or_params* p);
  * C_init (row-major [ny][nx]) are given.  History = (T u, C u) at t = 0. */
 or_state* or_create(const or_params* p, uint64_t seed, double noise,
                     const double* T_init, const double* C_init);
+/* The same with a porosity field eps[ny][nx] and a permeability field K[ny][nx]
+ * (either may be NULL: then p->eps / p->K everywhere).  At every node the model of
+ * Sec. 2-3 is applied with that node's eps, K and F_eps = 1.75 / sqrt(150 eps^3)
+ * (Eq. 7), i.e. the REV model with spatially varying porous properties. */
+or_state* or_create_field(const or_params* p, uint64_t seed, double noise, const double* T_init,
+                          const double* C_init, const double* eps, const double* K);
 void or_destroy(or_state* s);
 
 /* n time steps: collide (Eqs. 10, 21, 22), stream (Eq. 11), wall rules. */

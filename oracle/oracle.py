@@ -73,6 +73,8 @@ def lib():
             L.or_derive.restype = C.c_int
             L.or_create.argtypes = [P, C.c_uint64, C.c_double, dp, dp]
             L.or_create.restype = C.c_void_p
+            L.or_create_field.argtypes = [P, C.c_uint64, C.c_double, dp, dp, dp, dp]
+            L.or_create_field.restype = C.c_void_p
             L.or_destroy.argtypes = [C.c_void_p]
             L.or_step.argtypes = [C.c_void_p, C.c_long]
             L.or_time.argtypes = [C.c_void_p]
@@ -160,13 +162,14 @@ def uniform(seed: int, k: int) -> float:
 class Oracle:
     """One cavity state advanced by the FP64 oracle."""
 
-    def __init__(self, p: Params, seed: int = 1, noise: float = 1e-3, T_init=None, C_init=None):
+    def __init__(self, p: Params, seed: int = 1, noise: float = 1e-3, T_init=None, C_init=None,
+                 eps_field=None, K_field=None):
         self.p = p
         self.nx, self.ny = p.nx, p.ny
-        Ti = None if T_init is None else np.ascontiguousarray(T_init, dtype=np.float64)
-        Ci = None if C_init is None else np.ascontiguousarray(C_init, dtype=np.float64)
-        self._keep = (Ti, Ci)
-        self.h = lib().or_create(C.byref(p), C.c_uint64(seed), noise, _ptr(Ti), _ptr(Ci))
+        arr = [None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+               for a in (T_init, C_init, eps_field, K_field)]
+        self._keep = arr
+        self.h = lib().or_create_field(C.byref(p), C.c_uint64(seed), noise, *[_ptr(a) for a in arr])
         if not self.h:
             raise MemoryError("or_create failed")
 

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_launch.h"
@@ -81,6 +82,9 @@ Coef<R> make_coef(const lbm_params& P) {
     c.dirichlet_mask = (P.wall_lr == LBM_WALL_DIRICHLET ? 3 : 0) |
                        (P.wall_tb == LBM_WALL_DIRICHLET ? 12 : 0);
     c.sr = 1;
+    c.poro = nullptr;
+    c.nu = (R)P.nu;
+    c.varpi5 = (R)(5.0 * P.varpi);
     c.moving = 0;
     for (int s = 0; s < 4; ++s)
         for (int d = 0; d < 2; ++d) {
@@ -131,6 +135,7 @@ struct lbm_ctx {
     double* d_snap = nullptr;       // lazily allocated [4][ny][nx]
     double* d_partial = nullptr;    // lazily allocated residual partials
     double* d_stage = nullptr;      // lazily allocated [2][ny][nx] initial-field staging
+    void* poro = nullptr;           // optional [2][ny][pitch] (eps, K) in the compute precision
     bool snap_valid = false;
     int cur = 0;                    // two-buffer layout: buffer holding the state
     int64_t t = 0;
@@ -521,6 +526,57 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
     if (c->layout == LBM_AB_PULL) c->buf[1] = c->dalloc(c->state_bytes());
     c->hist = c->dalloc(c->hist_bytes());
     c->d_out = (double*)c->dalloc(64 * sizeof(double));
+    if (O.eps_field || O.K_field) {
+        if (c->P.model_a) {
+            lbm_status s = c->fail(LBM_ERR_INVALID, "lbm_create: porous fields are not supported with model_a");
+            g_last_error = c->err;
+            lbm_destroy(c);
+            return s;
+        }
+        // both planes in the compute precision, row pitch of the state
+        const size_t plane = c->G.plane, n2 = 2 * plane;
+        std::vector<double> hv(n2, 0.0);
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const size_t k = (size_t)j * nx + i, d = (size_t)j * c->G.pitch + i;
+                const double e = O.eps_field ? O.eps_field[k] : c->P.eps;
+                const double K = O.K_field ? O.K_field[k] : c->P.K;
+                if (!(e > 0.0 && e <= 1.0) || !(K > 0.0)) {
+                    lbm_status s = c->fail(LBM_ERR_INVALID,
+                                           "lbm_create: porous field at (%d, %d): eps %g, K %g", i, j, e, K);
+                    g_last_error = c->err;
+                    lbm_destroy(c);
+                    return s;
+                }
+                hv[d] = e;
+                hv[plane + d] = K;
+            }
+        // padding columns: copies of a valid value, never read by the kernels
+        for (size_t d = 0; d < n2; ++d)
+            if (hv[d] == 0.0) hv[d] = d < plane ? c->P.eps : c->P.K;
+        c->poro = c->dalloc(n2 * c->rsz);
+        if (!c->poro) {
+            lbm_status s = c->fail(LBM_ERR_NOMEM, "lbm_create: no device memory for the porous field");
+            g_last_error = c->err;
+            lbm_destroy(c);
+            return s;
+        }
+        cudaError_t e;
+        if (c->rsz == 8) {
+            e = cudaMemcpy(c->poro, hv.data(), n2 * 8, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> hf(hv.begin(), hv.end());
+            e = cudaMemcpy(c->poro, hf.data(), n2 * 4, cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) {
+            lbm_status s = c->cuda_fail(e, "lbm_create: porous field upload");
+            g_last_error = c->err;
+            lbm_destroy(c);
+            return s;
+        }
+        c->cd.poro = c->rsz == 8 ? (const double*)c->poro : nullptr;
+        c->cf.poro = c->rsz == 4 ? (const float*)c->poro : nullptr;
+    }
     if (!c->buf[0] || (c->layout == LBM_AB_PULL && !c->buf[1]) || !c->hist || !c->d_out) {
         lbm_status s = c->fail(LBM_ERR_NOMEM, "lbm_create: device allocation of %.3f GB failed",
                                (2.0 * c->state_bytes() + c->hist_bytes()) / 1e9);
@@ -844,6 +900,8 @@ lbm_status lbm_load(lbm_ctx* c, const void* buf, size_t len) {
     c->cd = make_coef<double>(c->P);
     c->cf = make_coef<float>(c->P);
     c->cf.sr = c->round_nearest ? 0 : 1;
+    c->cd.poro = (c->poro && c->rsz == 8) ? (const double*)c->poro : nullptr;
+    c->cf.poro = (c->poro && c->rsz == 4) ? (const float*)c->poro : nullptr;
     if (c->graph) {   // constants are baked into the captured launches
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
@@ -878,6 +936,7 @@ void lbm_destroy(lbm_ctx* c) {
     c->dfree(c->d_snap, 4 * c->nodes() * sizeof(double));
     c->dfree(c->d_partial, (size_t)residual_blocks(c->G) * 9 * sizeof(double));
     c->dfree(c->d_stage, 2 * c->nodes() * sizeof(double));
+    c->dfree(c->poro, 2 * c->G.plane * c->rsz);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -147,11 +147,35 @@ struct Coef {
     // Moving walls: wmom[s] = 2 rho0 u_w / c_s^2 of side s; moving = 1 if any is nonzero.
     R wmom[4][2];
     int moving;
+    // Spatially varying porous medium: NULL, or planes [2][ny][pitch] of (eps, K); then
+    // the porous constants above are recomputed per node (porous_at).
+    const R* poro;
+    R nu, varpi5;              // fluid viscosity of Eq. 5, 5 varpi of Eq. 25
 };
+
 
 template <typename R> __device__ __forceinline__ R sqrt_(R x);
 template <> __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+
+// The constants of node `self` of a cavity with a porosity / permeability field:
+// eps and K from the field, F_eps from Eq. 7, l0 and l1 from Eq. 19, the drag
+// coefficients of Eq. 5 and the n_eq,3 factor of Eq. 25.
+template <typename R>
+__device__ __forceinline__ void porous_at(Coef<R>& c, size_t self, size_t plane) {
+    const R e = c.poro[self], K = c.poro[plane + self];
+    const R Fe = R(1.75) / sqrt_(R(150) * e * e * e);
+    c.eps = e;
+    c.half_eps = R(0.5) * e;
+    c.inv_eps = R(1) / e;
+    c.inv_eps_f = c.inv_eps;
+    c.drag_lin = e * c.nu / K;
+    c.drag_quad = e * Fe / sqrt_(K);
+    c.l0 = R(0.5) * (R(1) + R(0.5) * c.drag_lin);
+    c.l0sq = c.l0 * c.l0;
+    c.l1 = R(0.5) * c.drag_quad;
+    c.c3C = c.varpi5 - R(4) * e;
+}
 
 // Macroscopic quantities of one node from pre-collision deviations.
 template <typename R>

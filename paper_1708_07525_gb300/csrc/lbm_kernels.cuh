@@ -198,7 +198,13 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
     gather_pull<false, true>(src, G, i, j, c, f, g, h);
     load_hist(hist, G, self, hv);
     uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
-    collide(c, f, g, h, hv);
+    if (c.poro) {
+        Coef<R> cl = c;
+        porous_at(cl, self, G.plane);
+        collide(cl, f, g, h, hv);
+    } else {
+        collide(c, f, g, h, hv);
+    }
     store_ab(dst, G, self, c, f, g, h, seed);
     store_hist(hist, G, self, hv);
 }
@@ -227,7 +233,13 @@ step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, G
         gather_local<true>(buf, G, i, j, f, g, h);
     load_hist(hist, G, self, hv);
     uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
-    collide(c, f, g, h, hv);
+    if (c.poro) {
+        Coef<R> cl = c;
+        porous_at(cl, self, G.plane);
+        collide(cl, f, g, h, hv);
+    } else {
+        collide(c, f, g, h, hv);
+    }
     if (ODD)
         store_aa_odd(buf, G, i, j, self, c, f, g, h, seed);
     else
@@ -273,6 +285,8 @@ __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restr
     const size_t self = (size_t)j * G.pitch + i;
     double Tp, Cp;
     initial_TC(I, G, i, j, Tp, Cp);
+    // porosity of this node (the h rest equilibrium depends on it, Eq. 28)
+    const double eps_n = c.poro ? (double)c.poro[self] : I.eps;
     // flow at rest: f' = 0; in the pull layout a slot whose link leaves the cavity holds
     // the value the moving-wall rule turns into 0 (wall_momentum of that wall).
 #pragma unroll
@@ -288,19 +302,20 @@ __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restr
         double vg, vh;
         if (!PULL) {
             vg = eq5_dev(q, I.sigma, I.varpi, Tp, I.model_a);
-            vh = eq5_dev(q, I.eps, I.varpi, Cp, I.model_a);
+            vh = eq5_dev(q, eps_n, I.varpi, Cp, I.model_a);
         } else {
             const int ti = i + ex_of(q), tj = j + ey_of(q);
             if ((unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny) {
                 double Tn, Cn;
                 initial_TC(I, G, ti, tj, Tn, Cn);
+                const double eps_t = c.poro ? (double)c.poro[(size_t)tj * G.pitch + ti] : I.eps;
                 vg = eq5_dev(q, I.sigma, I.varpi, Tn, I.model_a);
-                vh = eq5_dev(q, I.eps, I.varpi, Cn, I.model_a);
+                vh = eq5_dev(q, eps_t, I.varpi, Cn, I.model_a);
             } else {
                 // pulled back at y along opp(q) through the wall ahead of q
                 const int o = opp_of(q), side = pull_side(o);
                 const double wg = eq5_dev(o, I.sigma, I.varpi, Tp, I.model_a);
-                const double wh = eq5_dev(o, I.eps, I.varpi, Cp, I.model_a);
+                const double wh = eq5_dev(o, eps_n, I.varpi, Cp, I.model_a);
                 const bool dir = (c.dirichlet_mask >> side) & 1;
                 vg = dir ? (double)c.wallT[side] - wg : wg;
                 vh = dir ? (double)c.wallC[side] - wh : wh;
@@ -316,9 +331,11 @@ __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restr
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         g[q] = (R)eq5_dev(q, I.sigma, I.varpi, Tp, I.model_a);
-        h[q] = (R)eq5_dev(q, I.eps, I.varpi, Cp, I.model_a);
+        h[q] = (R)eq5_dev(q, eps_n, I.varpi, Cp, I.model_a);
     }
-    Macro<R> M = macro(c, f, g, h);
+    Coef<R> cl = c;
+    if (c.poro) porous_at(cl, self, G.plane);
+    Macro<R> M = macro(cl, f, g, h);
     R hv[4];
     const R T = c.T0 + M.Tp, C = c.C0 + M.Cp;
     hv[0] = T * M.ux;
@@ -341,7 +358,9 @@ __global__ void fields_kernel(const S* __restrict__ buf, Geom G, Coef<typename R
     const int i = x0 + wi, j = y0 + wj;
     R f[9], g[5], hh[5];
     gather<true>(mode, buf, G, i, j, c, f, g, hh);
-    Macro<R> M = macro(c, f, g, hh);
+    Coef<R> cl = c;
+    if (c.poro) porous_at(cl, (size_t)j * G.pitch + i, G.plane);
+    Macro<R> M = macro(cl, f, g, hh);
     const size_t n = (size_t)w * h, k = (size_t)wj * w + wi;
     out[k] = (double)M.ux;
     out[n + k] = (double)M.uy;
@@ -378,8 +397,9 @@ nush_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c, i
             gather<false>(mode, buf, G, cols[k], j, c, f, g, h);
             const R sg = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
             const R sh = ((h[0] + h[1]) + (h[2] + h[3])) + h[4];
+            const R ie = c.poro ? R(1) / c.poro[(size_t)j * G.pitch + cols[k]] : c.inv_eps;
             T[k] = W.T0 + (double)(sg * c.inv_sigma);
-            C[k] = W.C0 + (double)(sh * c.inv_eps);
+            C[k] = W.C0 + (double)(sh * ie);
         }
         // dPhi/dx at the wall: (-8 Phi_w + 9 Phi_0 - Phi_1) / 3, mirrored on the right
         acc[0] += -W.L * (-8.0 * W.Tw[0] + 9.0 * T[0] - T[1]) / 3.0 / W.dT;
@@ -419,8 +439,9 @@ nush_tb_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c
             gather<false>(mode, buf, G, i, rows[k], c, f, g, h);
             const R sg = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
             const R sh = ((h[0] + h[1]) + (h[2] + h[3])) + h[4];
+            const R ie = c.poro ? R(1) / c.poro[(size_t)rows[k] * G.pitch + i] : c.inv_eps;
             T[k] = W.T0 + (double)(sg * c.inv_sigma);
-            C[k] = W.C0 + (double)(sh * c.inv_eps);
+            C[k] = W.C0 + (double)(sh * ie);
         }
         // dPhi/dy at the wall through the wall value and the first two rows
         acc[0] += W.L * (-8.0 * W.Tw[0] + 9.0 * T[0] - T[1]) / 3.0 / W.dT;
@@ -458,7 +479,9 @@ residual_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> 
         const int j = (int)(k / G.nx), i = (int)(k - (size_t)j * G.nx);
         R f[9], g[5], h[5];
         gather<true>(mode, buf, G, i, j, c, f, g, h);
-        Macro<R> M = macro(c, f, g, h);
+        Coef<R> cl = c;
+        if (c.poro) porous_at(cl, (size_t)j * G.pitch + i, G.plane);
+        Macro<R> M = macro(cl, f, g, h);
         const double phi[4] = {(double)M.ux, (double)M.uy, (double)c.T0 + (double)M.Tp,
                                (double)c.C0 + (double)M.Cp};
 #pragma unroll

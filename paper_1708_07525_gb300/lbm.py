@@ -48,6 +48,7 @@ class lbm_options(C.Structure):
         ("T_init", C.POINTER(C.c_double)), ("C_init", C.POINTER(C.c_double)),
         ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
         ("block_x", C.c_int), ("block_y", C.c_int), ("graph_chunk", C.c_int),
+        ("eps_field", C.POINTER(C.c_double)), ("K_field", C.POINTER(C.c_double)),
         ("round_nearest", C.c_int),
     ]
 
@@ -183,7 +184,7 @@ class Cavity:
                  J=1.0, sigma=1.0, *, params: lbm_params | None = None, precision="f64",
                  layout="ab", Ma=0.0, varpi=0.0, seed=1, noise=1e-3, T_init=None, C_init=None,
                  stream=None, allocator="torch", block=(0, 0), graph_chunk=0,
-                 round_nearest=False):
+                 round_nearest=False, eps_field=None, K_field=None):
         L = lib()
         o = lbm_options()
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -204,6 +205,11 @@ class Cavity:
         o.block_x, o.block_y = int(block[0]), int(block[1])
         o.graph_chunk = int(graph_chunk)
         o.round_nearest = int(bool(round_nearest))
+        for name, arr in (("eps_field", eps_field), ("K_field", K_field)):
+            if arr is not None:
+                a = np.ascontiguousarray(arr, dtype=np.float64)
+                self._keep.append(a)
+                setattr(o, name, _dptr(a))
         h = C.c_void_p()
         if params is not None:
             st = L.lbm_create_raw(C.byref(params), C.byref(o), C.byref(h))

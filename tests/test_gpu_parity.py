@@ -209,3 +209,42 @@ def test_model_a_f64_against_oracle(oracle_mod, layout):
     gpu.step(1000)
     ora.step(1000)
     compare(gpu, ora, 1e-12, nush_tol=1e-11)
+
+
+def smooth_fields(nx, ny, seed):
+    """A porosity field in [0.45, 0.95] and a permeability field within a factor 3 of
+    each other, smooth in space (sum of a few seeded Fourier modes)."""
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:ny, 0:nx] + 0.5
+    e = np.zeros((ny, nx))
+    k = np.zeros((ny, nx))
+    for _ in range(3):
+        a, b, ph = rng.uniform(0.5, 2.5, 3)
+        e += np.sin(2 * np.pi * (a * x / nx + b * y / ny) + ph)
+        k += np.cos(2 * np.pi * (b * x / nx - a * y / ny) + ph)
+    eps = 0.7 + 0.25 * e / np.abs(e).max()
+    K = 0.01 * nx * nx * np.exp(0.55 * k / np.abs(k).max())
+    return eps, K
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_porous_fields_against_oracle(oracle_mod, precision, tol, layout):
+    spec = CavitySpec(48, 37, Ra=5e4, Da=1e-2, eps=0.6, Le=3.0, N=-1.5, sigma=1.3, seed=21,
+                      noise=0.02)
+    eps, K = smooth_fields(spec.nx, spec.ny, seed=3)
+    gpu = lbm.Cavity(*spec.args(), precision=precision, layout=layout, seed=spec.seed,
+                     noise=spec.noise, eps_field=eps, K_field=K)
+    ora = oracle_mod.Oracle(oracle_mod.derive(*spec.args()), seed=spec.seed, noise=spec.noise,
+                            eps_field=eps, K_field=K)
+    gpu.step(1000)
+    ora.step(1000)
+    compare(gpu, ora, tol, nush_tol=(1e-11 if precision == "f64" else None))
+
+
+def test_porous_field_rejects_bad_values():
+    eps = np.full((16, 16), 0.5)
+    eps[3, 4] = 1.5
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Cavity(16, 16, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0, eps_field=eps)
+    assert ei.value.status == lbm.ERR_INVALID and "(4, 3)" in str(ei.value)
