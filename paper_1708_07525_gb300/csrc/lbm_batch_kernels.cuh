@@ -67,7 +67,7 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
             if (!AA) {
                 const S* src = (const S*)I.buf[odd];
                 S* dst = (S*)I.buf[odd ^ 1];
-                gather_pull<false, true>(src, G, i, j, I.c, f, g, h);
+                gather_pull<false, true, false>(src, G, i, j, I.c, f, g, h);
                 load_hist(hist, G, self, hv);
                 uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
                 collide(I.c, f, g, h, hv);
@@ -75,14 +75,14 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
             } else {
                 S* buf = (S*)I.buf[0];
                 if (odd)
-                    gather_pull<true, true>(buf, G, i, j, I.c, f, g, h);
+                    gather_pull<true, true, false>(buf, G, i, j, I.c, f, g, h);
                 else
                     gather_local<true>(buf, G, i, j, f, g, h);
                 load_hist(hist, G, self, hv);
                 uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
                 collide(I.c, f, g, h, hv);
                 if (odd)
-                    store_aa_odd(buf, G, i, j, self, I.c, f, g, h, seed);
+                    store_aa_odd<false>(buf, G, i, j, self, I.c, f, g, h, seed);
                 else
                     store_aa_even(buf, G, self, I.c, f, g, h, seed);
             }
@@ -118,7 +118,7 @@ batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
     if (!AA) {
         const S* src = (const S*)I.buf[odd];
         S* dst = (S*)I.buf[odd ^ 1];
-        gather_pull<false, true>(src, G, i, j, I.c, f, g, h);
+        gather_pull<false, true, false>(src, G, i, j, I.c, f, g, h);
         load_hist(hist, G, self, hv);
         uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
         collide(I.c, f, g, h, hv);
@@ -126,14 +126,14 @@ batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
     } else {
         S* buf = (S*)I.buf[0];
         if (odd)
-            gather_pull<true, true>(buf, G, i, j, I.c, f, g, h);
+            gather_pull<true, true, false>(buf, G, i, j, I.c, f, g, h);
         else
             gather_local<true>(buf, G, i, j, f, g, h);
         load_hist(hist, G, self, hv);
         uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
         collide(I.c, f, g, h, hv);
         if (odd)
-            store_aa_odd(buf, G, i, j, self, I.c, f, g, h, seed);
+            store_aa_odd<false>(buf, G, i, j, self, I.c, f, g, h, seed);
         else
             store_aa_even(buf, G, self, I.c, f, g, h, seed);
     }

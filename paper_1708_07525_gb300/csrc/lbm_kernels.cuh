@@ -42,7 +42,9 @@ __device__ __forceinline__ R wall_momentum(const Coef<R>& c, int side, int q) {
 // t-1 post-collision values (pull streaming, Eq. 11, with the halfway wall
 // rules).  SWAP = false: two-buffer layout, slot q of the source node.
 // SWAP = true: in-place AA layout after an even step, slot opp(q) of the source.
-template <bool SWAP, bool WITH_F, typename S, typename R>
+// EXT: the cavity may have moving walls (checked at run time); without it the
+// moving-wall code is not compiled in (the fast path of the plain cavity).
+template <bool SWAP, bool WITH_F, bool EXT = true, typename S, typename R>
 __device__ __forceinline__ void gather_pull(const S* __restrict__ buf, const Geom& G, int i, int j,
                                             const Coef<R>& c, R f[9], R g[5], R h[5]) {
     const size_t self = (size_t)j * G.pitch + i;
@@ -56,7 +58,7 @@ __device__ __forceinline__ void gather_pull(const S* __restrict__ buf, const Geo
             const S* p = in ? buf + (size_t)(QF + slot_src) * G.plane + (size_t)sj * G.pitch + si
                             : buf + (size_t)(QF + slot_self) * G.plane + self;
             f[q] = Store<S>::ld(p);   // halfway bounce-back when !in
-            if (!in && c.moving) f[q] += wall_momentum(c, link_side(si, sj, G), q);
+            if (EXT && !in && c.moving) f[q] += wall_momentum(c, link_side(si, sj, G), q);
         }
     }
 #pragma unroll
@@ -150,7 +152,7 @@ __device__ __forceinline__ void store_aa_even(S* __restrict__ buf, const Geom& G
 
 // In-place layout, odd step: slot q of the neighbour x + e_q, or, where that link
 // crosses a wall, the wall rule's value in slot opp(q) of the node itself.
-template <typename S, typename R>
+template <bool EXT = true, typename S, typename R>
 __device__ __forceinline__ void store_aa_odd(S* __restrict__ buf, const Geom& G, int i, int j,
                                              size_t self, const Coef<R>& c, const R f[9],
                                              const R g[5], const R h[5], uint32_t& seed) {
@@ -161,7 +163,7 @@ __device__ __forceinline__ void store_aa_odd(S* __restrict__ buf, const Geom& G,
         S* p = in ? buf + (size_t)(QF + q) * G.plane + (size_t)tj * G.pitch + ti
                   : buf + (size_t)(QF + opp_of(q)) * G.plane + self;
         R v = f[q];
-        if (!in && c.moving) v -= wall_momentum(c, link_side(ti, tj, G), q);
+        if (EXT && !in && c.moving) v -= wall_momentum(c, link_side(ti, tj, G), q);
         put(p, v, c.sr, seed, q);
     }
 #pragma unroll
@@ -183,8 +185,23 @@ __device__ __forceinline__ void store_aa_odd(S* __restrict__ buf, const Geom& G,
     }
 }
 
+// Collision with the node's own porous constants when the cavity has a porous field
+// (EXT builds only; the plain cavity's kernel compiles one collision).
+template <bool EXT, typename R>
+__device__ __forceinline__ void collide_node(const Coef<R>& c, size_t self, size_t plane, R f[9],
+                                             R g[5], R h[5], R hv[4]) {
+    if (EXT && c.poro) {
+        Coef<R> cl = c;
+        porous_at(cl, self, plane);
+        collide(cl, f, g, h, hv);
+    } else {
+        collide(c, f, g, h, hv);
+    }
+}
+
 // ---- the fused step, two-buffer pull layout ---------------------------------------
-template <typename S>
+// EXT = true for cavities with moving walls or porous fields, false otherwise.
+template <typename S, bool EXT>
 __global__ void __launch_bounds__(256)
 step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
                typename Real<S>::type* __restrict__ hist, Geom G,
@@ -195,16 +212,10 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
     if (i >= G.nx || j >= G.ny) return;
     R f[9], g[5], h[5], hv[4];
     const size_t self = (size_t)j * G.pitch + i;
-    gather_pull<false, true>(src, G, i, j, c, f, g, h);
+    gather_pull<false, true, EXT>(src, G, i, j, c, f, g, h);
     load_hist(hist, G, self, hv);
     uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
-    if (c.poro) {
-        Coef<R> cl = c;
-        porous_at(cl, self, G.plane);
-        collide(cl, f, g, h, hv);
-    } else {
-        collide(c, f, g, h, hv);
-    }
+    collide_node<EXT>(c, self, G.plane, f, g, h, hv);
     store_ab(dst, G, self, c, f, g, h, seed);
     store_hist(hist, G, self, hv);
 }
@@ -217,7 +228,7 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
 // (or, where that link crosses a wall, the reflected value into slot opp(q)
 // of x).  Each thread reads and writes the same set of locations, so the
 // update is race-free in place.
-template <typename S, bool ODD>
+template <typename S, bool ODD, bool EXT>
 __global__ void __launch_bounds__(256)
 step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
                Coef<typename Real<S>::type> c) {
@@ -228,20 +239,14 @@ step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, G
     R f[9], g[5], h[5], hv[4];
     const size_t self = (size_t)j * G.pitch + i;
     if (ODD)
-        gather_pull<true, true>(buf, G, i, j, c, f, g, h);
+        gather_pull<true, true, EXT>(buf, G, i, j, c, f, g, h);
     else
         gather_local<true>(buf, G, i, j, f, g, h);
     load_hist(hist, G, self, hv);
     uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
-    if (c.poro) {
-        Coef<R> cl = c;
-        porous_at(cl, self, G.plane);
-        collide(cl, f, g, h, hv);
-    } else {
-        collide(c, f, g, h, hv);
-    }
+    collide_node<EXT>(c, self, G.plane, f, g, h, hv);
     if (ODD)
-        store_aa_odd(buf, G, i, j, self, c, f, g, h, seed);
+        store_aa_odd<EXT>(buf, G, i, j, self, c, f, g, h, seed);
     else
         store_aa_even(buf, G, self, c, f, g, h, seed);
     store_hist(hist, G, self, hv);

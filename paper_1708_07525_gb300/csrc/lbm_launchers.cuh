@@ -26,7 +26,10 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
                            const Coef<typename Real<S>::type>& c, const LaunchCfg& L) {
     using R = typename Real<S>::type;
     dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
-    step_ab_kernel<S><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+    if (c.poro || c.moving)
+        step_ab_kernel<S, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+    else
+        step_ab_kernel<S, false><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
     return cudaGetLastError();
 }
 
@@ -35,10 +38,15 @@ cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
                            const Coef<typename Real<S>::type>& c, bool odd, const LaunchCfg& L) {
     using R = typename Real<S>::type;
     dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
-    if (odd)
-        step_aa_kernel<S, true><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+    const bool ext = c.poro || c.moving;
+    if (odd && ext)
+        step_aa_kernel<S, true, true><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+    else if (odd)
+        step_aa_kernel<S, true, false><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+    else if (ext)
+        step_aa_kernel<S, false, true><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
     else
-        step_aa_kernel<S, false><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+        step_aa_kernel<S, false, false><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
     return cudaGetLastError();
 }
 
