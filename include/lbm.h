@@ -214,7 +214,10 @@ lbm_status lbm_nusselt_sherwood_tb(lbm_ctx* ctx, double out[4]);
 /* Steady-state residual: r = max over phi in {u_x, u_y, T, C} of
  * max|phi_now - phi_snap| / max|phi_now|, where phi_snap is the snapshot of
  * the previous call (r = +inf on the first call); the snapshot is then
- * replaced by phi_now.  Reduced in FP64.  Synchronises the stream.
+ * replaced by phi_now.  Per node the differences are taken in the compute
+ * precision (FP64 for FP64 storage, else FP32) on u_x, u_y, T - T0 and C - C0,
+ * so that the difference of two close values is exact; the maxima and the
+ * ratio are reduced in FP64.  Synchronises the stream.
  * LBM_ERR_DIVERGED if a field value is not finite. */
 lbm_status lbm_residual(lbm_ctx* ctx, double* r);
 
@@ -357,9 +360,8 @@ lbm_status lbm_server_info(const lbm_server* s, int* queued, int* active, int* d
 void lbm_server_destroy(lbm_server* s);
 const char* lbm_server_last_error(const lbm_server* s);
 
-/* Largest grid lbm_residual_noalloc() accepts, set by its fixed scratch array. */
+/* Slots of 9 doubles in the fixed scratch of lbm_residual_noalloc(). */
 #define LBM_NOALLOC_MAX_BLOCKS 4096
-#define LBM_NOALLOC_MAX_NODES (LBM_NOALLOC_MAX_BLOCKS * 1024)
 
 /* The steady-state residual of lbm_residual(), for callers that cannot let the
  * library allocate device memory when they ask for it: code embedded in a host
@@ -367,19 +369,19 @@ const char* lbm_server_last_error(const lbm_server* s);
  * loops that must not stall, since cudaMalloc and cudaFree can synchronise
  * the whole device.  The paper has no counterpart; this is plumbing.
  *   snapshot       caller-owned device buffer of 4 * nx * ny doubles, planes
- *                  (u_x, u_y, T, C) of [ny][nx]; read as the previous snapshot
- *                  and overwritten with the current fields.
+ *                  (u_x, u_y, T - T0, C - C0) of [ny][nx] (values of the compute
+ *                  precision); read as the previous snapshot and overwritten
+ *                  with the current fields.
  *   have_snapshot  0 if snapshot holds no earlier fields (then *r = +inf).
  *   r              host output, defined as in lbm_residual().
- * Allocates nothing: the per-block maxima live in one file-scope device array
- * of LBM_NOALLOC_MAX_BLOCKS * 9 + 16 doubles (about 288 KiB), which every GPU
- * that loads the library holds until the process exits.  Grids of more than
- * LBM_NOALLOC_MAX_NODES nodes are rejected with LBM_ERR_INVALID.  The first
- * call on each device looks up the array's device address; make that first
- * call before any stream capture.  All calls share the array and it keeps the
- * last call's contents (each call writes every slot it reads, so nothing has
- * to be cleared); calls whose work overlaps on the GPU, from any context or
- * stream, race on it.  Synchronises the context's stream.  Errors as for
+ * Allocates nothing: the per-block maxima are folded into one file-scope
+ * device array of LBM_NOALLOC_MAX_BLOCKS * 9 + 16 doubles (about 288 KiB), which
+ * every GPU that loads the library holds until the process exits; any grid fits
+ * (the blocks of the first pass share its slots).  The first call on each
+ * device looks up the array's device address; make that first call before any
+ * stream capture.  All calls share the array: each call clears it, then folds
+ * into it; calls whose work overlaps on the GPU, from any context or stream,
+ * race on it.  Synchronises the context's stream.  Errors as for
  * lbm_residual(), plus LBM_ERR_INVALID for NULL arguments. */
 lbm_status lbm_residual_noalloc(lbm_ctx* ctx, double* snapshot, int have_snapshot, double* r);
 

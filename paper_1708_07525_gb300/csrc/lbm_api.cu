@@ -132,7 +132,7 @@ struct lbm_ctx {
     double* d_out = nullptr;        // 16 doubles: Nu/Sh and residual results
     double* d_fields = nullptr;     // lazily allocated [5][h][w] read-out window
     size_t fields_cap = 0;          // nodes d_fields holds
-    double* d_snap = nullptr;       // lazily allocated [4][ny][nx]
+    void* d_snap = nullptr;         // lazily allocated [4][ny][nx] in the compute precision
     double* d_partial = nullptr;    // lazily allocated residual partials
     double* d_stage = nullptr;      // lazily allocated [2][ny][nx] initial-field staging
     void* poro = nullptr;           // optional [2][ny][pitch] (eps, K) in the compute precision
@@ -799,10 +799,9 @@ lbm_status lbm_residual(lbm_ctx* c, double* r) {
     }
     DeviceGuard dg(c->device);
     const size_t n = c->nodes();
-    const int nb = residual_blocks(c->G);
     if (!c->d_snap) {
-        c->d_snap = (double*)c->dalloc(4 * n * sizeof(double));
-        c->d_partial = (double*)c->dalloc((size_t)nb * 9 * sizeof(double));
+        c->d_snap = c->dalloc(4 * n * c->rsz);
+        c->d_partial = (double*)c->dalloc((size_t)RES_SLOTS * 9 * sizeof(double));
         if (!c->d_snap || !c->d_partial) return c->fail(LBM_ERR_NOMEM, "lbm_residual: no device memory");
     }
     const int mode = c->read_mode();
@@ -933,8 +932,8 @@ void lbm_destroy(lbm_ctx* c) {
     c->dfree(c->hist, c->hist_bytes());
     c->dfree(c->d_out, 64 * sizeof(double));
     c->dfree(c->d_fields, 5 * c->fields_cap * sizeof(double));
-    c->dfree(c->d_snap, 4 * c->nodes() * sizeof(double));
-    c->dfree(c->d_partial, (size_t)residual_blocks(c->G) * 9 * sizeof(double));
+    c->dfree(c->d_snap, 4 * c->nodes() * c->rsz);
+    c->dfree(c->d_partial, (size_t)RES_SLOTS * 9 * sizeof(double));
     c->dfree(c->d_stage, 2 * c->nodes() * sizeof(double));
     c->dfree(c->poro, 2 * c->G.plane * c->rsz);
     if (c->own_stream) cudaStreamDestroy(c->stream);

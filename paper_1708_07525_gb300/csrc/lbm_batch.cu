@@ -48,11 +48,11 @@ Geom geom_for(int nx, int ny, int prec) {
     return G;
 }
 
-// Arena bytes of one cavity: state buffers, FP32 history, FP64 residual snapshot.
+// Arena bytes of one cavity: state buffers, FP32 history, FP32 residual snapshot.
 size_t inst_bytes(const Geom& G, int prec, int layout) {
     const size_t st = align_up((size_t)NQ * G.plane * esize(prec), 256);
     const size_t hi = align_up((size_t)4 * G.plane * sizeof(float), 256);
-    const size_t sn = align_up((size_t)4 * G.nx * G.ny * sizeof(double), 256);
+    const size_t sn = align_up((size_t)4 * G.nx * G.ny * sizeof(float), 256);
     return (layout == LBM_AA ? 1 : 2) * st + hi + sn;
 }
 
@@ -241,10 +241,10 @@ struct lbm_batch {
         const size_t st = align_up((size_t)NQ * s.G.plane * esize(prec), 256);
         return arena.base + s.off + (layout == LBM_AA ? 1 : 2) * st;
     }
-    double* slot_snap(const Slot& s) const {
+    float* slot_snap(const Slot& s) const {
         const size_t st = align_up((size_t)NQ * s.G.plane * esize(prec), 256);
         const size_t hi = align_up((size_t)4 * s.G.plane * sizeof(float), 256);
-        return (double*)(arena.base + s.off + (layout == LBM_AA ? 1 : 2) * st + hi);
+        return (float*)(arena.base + s.off + (layout == LBM_AA ? 1 : 2) * st + hi);
     }
     int parity() const { return (int)(t & 1); }
     int mode_of(const Slot& s) const {

@@ -15,7 +15,7 @@ template <typename R>
 struct alignas(16) BatchInst {
     void* buf[2];          // two-buffer layout: both; in-place layout: buf[0]
     void* hist;            // 4 history planes in R
-    double* snap;          // residual snapshot [4][ny][nx] (FP64) or NULL
+    R* snap;               // residual snapshot [4][ny][nx] (u_x, u_y, T - T0, C - C0) or NULL
     Geom G;
     Coef<R> c;
     int tile_w_log2;       // tile width = 1 << tile_w_log2 (32 .. 256)
@@ -160,13 +160,14 @@ batch_residual_kernel(const BatchInst<typename Real<S>::type>* __restrict__ tabl
                       double* __restrict__ partial) {
     using R = typename Real<S>::type;
     __shared__ BatchInst<R> I;
-    __shared__ double red[BATCH_THREADS / 32][9];
+    __shared__ R red[BATCH_THREADS / 32][9];
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         const int k = tile_owner[tile];
         __syncthreads();
         load_inst(table, k, I);
         __syncthreads();
-        double dmax[4] = {0, 0, 0, 0}, amax[4] = {0, 0, 0, 0}, bad = 0;
+        R dmax[4] = {0, 0, 0, 0}, amax[4] = {0, 0, 0, 0};
+        int bad = 0;
         if (I.active && I.snap) {
             const int local = tile - I.tile_begin;
             const int ty = local / I.tiles_x, tx = local - ty * I.tiles_x;
@@ -179,34 +180,41 @@ batch_residual_kernel(const BatchInst<typename Real<S>::type>* __restrict__ tabl
             for (int e = threadIdx.x; e < tw * I.tile_h; e += BATCH_THREADS) {
                 const int i = x0 + (e & (tw - 1)), j = y0 + (e >> I.tile_w_log2);
                 if (i >= G.nx || j >= G.ny) continue;
+                // snapshot loads first, stores last, as in lbm_residual's pass
+                const size_t kk = (size_t)j * G.nx + i;
+                R old[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) old[q] = I.snap[q * n + kk];
                 R f[9], g[5], h[5];
                 gather<true>(mode, buf, G, i, j, I.c, f, g, h);
                 Macro<R> M = macro(I.c, f, g, h);
-                const double phi[4] = {(double)M.ux, (double)M.uy, (double)I.c.T0 + (double)M.Tp,
-                                       (double)I.c.C0 + (double)M.Cp};
-                const size_t kk = (size_t)j * G.nx + i;
+                // differences in the compute precision on the deviations (exact for
+                // close values), as lbm_residual does
+                const R phi[4] = {M.ux, M.uy, M.Tp, M.Cp};
+                const R absv[4] = {M.ux, M.uy, I.c.T0 + M.Tp, I.c.C0 + M.Cp};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const double old = I.snap[q * n + kk];
-                    if (!isfinite(phi[q])) bad = 1;
-                    dmax[q] = fmax(dmax[q], fabs(phi[q] - old));
-                    amax[q] = fmax(amax[q], fabs(phi[q]));
-                    I.snap[q * n + kk] = phi[q];
+                    if (!finite_(phi[q])) bad = 1;
+                    dmax[q] = max_(dmax[q], abs_(phi[q] - old[q]));
+                    amax[q] = max_(amax[q], abs_(absv[q]));
                 }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) I.snap[q * n + kk] = phi[q];
             }
         }
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        double v[9] = {dmax[0], dmax[1], dmax[2], dmax[3], amax[0], amax[1], amax[2], amax[3], bad};
+        const R v[9] = {dmax[0], dmax[1], dmax[2], dmax[3], amax[0], amax[1], amax[2], amax[3],
+                        (R)bad};
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            const double r = warp_max(v[q]);
+            const R r = warp_max(v[q]);
             if (lane == 0) red[warp][q] = r;
         }
         __syncthreads();
         if (threadIdx.x < 9) {
-            double s = 0;
-            for (int w = 0; w < BATCH_THREADS / 32; ++w) s = fmax(s, red[w][threadIdx.x]);
-            partial[(size_t)tile * 9 + threadIdx.x] = s;
+            R s = 0;
+            for (int w = 0; w < BATCH_THREADS / 32; ++w) s = max_(s, red[w][threadIdx.x]);
+            partial[(size_t)tile * 9 + threadIdx.x] = (double)s;
         }
     }
 }

@@ -157,6 +157,17 @@ struct Coef {
 template <typename R> __device__ __forceinline__ R sqrt_(R x);
 template <> __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+// |x|, max(a, b) and finiteness in the precision of the argument (FP32 stays on the
+// FP32 pipes; GB300's FP64 pipe is narrow).
+template <typename R> __device__ __forceinline__ R abs_(R x);
+template <> __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+template <> __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+template <typename R> __device__ __forceinline__ R max_(R a, R b);
+template <> __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
+template <> __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+template <typename R> __device__ __forceinline__ bool finite_(R x);
+template <> __device__ __forceinline__ bool finite_(float x) { return fabsf(x) <= 3.402823466e38f; }
+template <> __device__ __forceinline__ bool finite_(double x) { return fabs(x) <= 1.7976931348623157e308; }
 
 // The constants of node `self` of a cavity with a porosity / permeability field:
 // eps and K from the field, F_eps from Eq. 7, l0 and l1 from Eq. 19, the drag

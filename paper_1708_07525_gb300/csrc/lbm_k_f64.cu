@@ -3,14 +3,6 @@
 
 namespace lbm {
 
-int residual_blocks(const Geom& G) {
-    const size_t n = (size_t)G.nx * G.ny;
-    size_t nb = (n + RES_THREADS - 1) / RES_THREADS;
-    // at most 8 resident blocks per SM on 152 SMs; the kernel is grid-stride
-    const size_t cap = 152 * 8;
-    return (int)(nb < cap ? nb : cap);
-}
-
 __global__ void __launch_bounds__(RES_THREADS)
 residual_final_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
     __shared__ double red[RES_THREADS / 32][9];

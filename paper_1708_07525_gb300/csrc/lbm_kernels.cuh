@@ -96,6 +96,18 @@ __device__ __forceinline__ void gather_local(const S* __restrict__ buf, const Ge
     }
 }
 
+// The same with the mode fixed at compile time (no code for the other two modes).
+template <int MODE, typename S, typename R>
+__device__ __forceinline__ void gather_m(const S* __restrict__ buf, const Geom& G, int i, int j,
+                                         const Coef<R>& c, R f[9], R g[5], R h[5]) {
+    if (MODE == GATHER_PULL_AB)
+        gather_pull<false, true>(buf, G, i, j, c, f, g, h);
+    else if (MODE == GATHER_PULL_AA)
+        gather_pull<true, true>(buf, G, i, j, c, f, g, h);
+    else
+        gather_local<true>(buf, G, i, j, f, g, h);
+}
+
 template <bool WITH_F, typename S, typename R>
 __device__ __forceinline__ void gather(int mode, const S* __restrict__ buf, const Geom& G, int i,
                                        int j, const Coef<R>& c, R f[9], R g[5], R h[5]) {
@@ -253,26 +265,35 @@ step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, G
 }
 
 // ---- initial state ---------------------------------------------------------------
-// T - T0 and C - C0 at t = 0: from caller arrays (FP64 [ny][nx]) or from the
-// SplitMix64 noise with key (field * ny + j) * nx + i.
-__device__ __forceinline__ void initial_TC(const InitSpec& I, const Geom& G, int i, int j,
-                                           double& Tp, double& Cp) {
+// T - T0 and C - C0 at t = 0 in the compute precision W: from caller arrays (FP64
+// [ny][nx]) or from the SplitMix64 noise with key (field * ny + j) * nx + i (in FP32
+// the uniform keeps the top 24 of its 53 bits, a change below 2^-24 of the noise).
+template <typename W>
+__device__ __forceinline__ W uniform_w(uint64_t seed, uint64_t k) {
+    if (sizeof(W) == sizeof(double)) return (W)uniform01(seed, k);
+    return (W)(uint32_t)(splitmix64_at(seed, k) >> 40) * W(1.0f / 16777216.0f);
+}
+
+template <typename W>
+__device__ __forceinline__ void initial_TC(const InitSpec& I, const Geom& G, int i, int j, W& Tp,
+                                           W& Cp) {
     const size_t k = (size_t)j * G.nx + i;
     if (I.T_init) {
-        Tp = I.T_init[k] - I.T0;
-        Cp = I.C_init[k] - I.C0;
+        Tp = (W)I.T_init[k] - (W)I.T0;
+        Cp = (W)I.C_init[k] - (W)I.C0;
     } else {
         const size_t n = (size_t)G.nx * G.ny;
-        Tp = I.noise * (2.0 * uniform01(I.seed, k) - 1.0);
-        Cp = I.noise * (2.0 * uniform01(I.seed, n + k) - 1.0);
+        Tp = (W)I.noise * (W(2) * uniform_w<W>(I.seed, k) - W(1));
+        Cp = (W)I.noise * (W(2) * uniform_w<W>(I.seed, n + k) - W(1));
     }
 }
 
 // Deviation of the D2Q5 rest equilibrium of Eq. 28 at u = 0 for Phi' = Phi - Phi0
 // (model A: w~_q cap Phi', from the velocity-space form of Eqs. 30-31).
-__device__ __forceinline__ double eq5_dev(int q, double cap, double varpi, double Pp, int model_a) {
-    if (model_a) return (q == 0 ? 1.0 - varpi : 0.25 * varpi) * cap * Pp;
-    return q == 0 ? (cap - varpi) * Pp : 0.25 * varpi * Pp;
+template <typename W>
+__device__ __forceinline__ W eq5_dev(int q, W cap, W varpi, W Pp, int model_a) {
+    if (model_a) return (q == 0 ? W(1) - varpi : W(0.25) * varpi) * cap * Pp;
+    return q == 0 ? (cap - varpi) * Pp : W(0.25) * varpi * Pp;
 }
 
 // Writes the state at t = 0.  AB (PULL = true): the buffer must give the t = 0
@@ -280,6 +301,7 @@ __device__ __forceinline__ double eq5_dev(int q, double cap, double varpi, doubl
 // y + e_q (or, for a link that leaves the cavity, the value whose wall rule
 // gives the t = 0 population of y).  AA (PULL = false): natural slots.
 // The flow populations are at rest (f' = 0).  History = (T u, C u) of t = 0.
+// Everything is computed in the compute precision R (FP64 or FP32).
 template <typename S, bool PULL>
 __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
                             Coef<typename Real<S>::type> c, InitSpec I) {
@@ -288,10 +310,11 @@ __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restr
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= G.nx || j >= G.ny) return;
     const size_t self = (size_t)j * G.pitch + i;
-    double Tp, Cp;
+    R Tp, Cp;
     initial_TC(I, G, i, j, Tp, Cp);
+    const R sig = (R)I.sigma, vp = (R)I.varpi;
     // porosity of this node (the h rest equilibrium depends on it, Eq. 28)
-    const double eps_n = c.poro ? (double)c.poro[self] : I.eps;
+    const R eps_n = c.poro ? c.poro[self] : (R)I.eps;
     // flow at rest: f' = 0; in the pull layout a slot whose link leaves the cavity holds
     // the value the moving-wall rule turns into 0 (wall_momentum of that wall).
 #pragma unroll
@@ -304,30 +327,30 @@ __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restr
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        double vg, vh;
+        R vg, vh;
         if (!PULL) {
-            vg = eq5_dev(q, I.sigma, I.varpi, Tp, I.model_a);
-            vh = eq5_dev(q, eps_n, I.varpi, Cp, I.model_a);
+            vg = eq5_dev(q, sig, vp, Tp, I.model_a);
+            vh = eq5_dev(q, eps_n, vp, Cp, I.model_a);
         } else {
             const int ti = i + ex_of(q), tj = j + ey_of(q);
             if ((unsigned)ti < (unsigned)G.nx && (unsigned)tj < (unsigned)G.ny) {
-                double Tn, Cn;
+                R Tn, Cn;
                 initial_TC(I, G, ti, tj, Tn, Cn);
-                const double eps_t = c.poro ? (double)c.poro[(size_t)tj * G.pitch + ti] : I.eps;
-                vg = eq5_dev(q, I.sigma, I.varpi, Tn, I.model_a);
-                vh = eq5_dev(q, eps_t, I.varpi, Cn, I.model_a);
+                const R eps_t = c.poro ? c.poro[(size_t)tj * G.pitch + ti] : (R)I.eps;
+                vg = eq5_dev(q, sig, vp, Tn, I.model_a);
+                vh = eq5_dev(q, eps_t, vp, Cn, I.model_a);
             } else {
                 // pulled back at y along opp(q) through the wall ahead of q
                 const int o = opp_of(q), side = pull_side(o);
-                const double wg = eq5_dev(o, I.sigma, I.varpi, Tp, I.model_a);
-                const double wh = eq5_dev(o, eps_n, I.varpi, Cp, I.model_a);
+                const R wg = eq5_dev(o, sig, vp, Tp, I.model_a);
+                const R wh = eq5_dev(o, eps_n, vp, Cp, I.model_a);
                 const bool dir = (c.dirichlet_mask >> side) & 1;
-                vg = dir ? (double)c.wallT[side] - wg : wg;
-                vh = dir ? (double)c.wallC[side] - wh : wh;
+                vg = dir ? c.wallT[side] - wg : wg;
+                vh = dir ? c.wallC[side] - wh : wh;
             }
         }
-        Store<S>::st(buf + (size_t)(QG + q) * G.plane + self, (R)vg);
-        Store<S>::st(buf + (size_t)(QH + q) * G.plane + self, (R)vh);
+        Store<S>::st(buf + (size_t)(QG + q) * G.plane + self, vg);
+        Store<S>::st(buf + (size_t)(QH + q) * G.plane + self, vh);
     }
     // history from the t = 0 macroscopic state (Eqs. 16-19, 26)
     R f[9], g[5], h[5];
@@ -335,8 +358,8 @@ __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restr
     for (int q = 0; q < 9; ++q) f[q] = R(0);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        g[q] = (R)eq5_dev(q, I.sigma, I.varpi, Tp, I.model_a);
-        h[q] = (R)eq5_dev(q, eps_n, I.varpi, Cp, I.model_a);
+        g[q] = eq5_dev(q, sig, vp, Tp, I.model_a);
+        h[q] = eq5_dev(q, eps_n, vp, Cp, I.model_a);
     }
     Coef<R> cl = c;
     if (c.poro) porous_at(cl, self, G.plane);
@@ -382,6 +405,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// FP32 maxima stay in FP32: GB300's FP64 pipe is narrow, and a per-block max in
+// FP64 (shuffle + fmax per step) made the residual pass FP64-bound.
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
@@ -469,49 +499,100 @@ nush_tb_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c
     }
 }
 
-// Residual pass 1: per node phi = (ux, uy, T, C) at the current level; per block
-// the maxima of |phi - snap| and |phi| and a non-finite flag go to
-// partial[block][9]; snap is replaced by phi.  Grid-stride over nodes.
-template <typename S>
+// Residual pass 1: per node phi = (u_x, u_y, T - T0, C - C0) at the current level
+// in the compute precision R (the deviations make the difference of two close
+// values exact); snap (element type P) is replaced by phi.  Each block reduces the
+// maxima of |phi - snap|, of |(u_x, u_y, T, C)| and a non-finite flag, and folds
+// them into slot (block index mod nslots) of slots[nslots][9] with an integer
+// atomicMax on the FP64 bit patterns (all values are >= 0, whose bit patterns
+// order as the values do); the slots must be zero before the launch.  Block
+// (bx, by) takes the 256-column tiles bx, bx + gridDim.x, ... of the rows by,
+// by + gridDim.y, ...; with the grid of residual_grid() that is one node per thread.
+template <typename S, bool EXT, typename P, int MODE>
 __global__ void __launch_bounds__(RES_THREADS)
-residual_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c, int mode,
-                double* __restrict__ snap, double* __restrict__ partial) {
+residual_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c,
+                P* __restrict__ snap, unsigned long long* __restrict__ slots, int nslots) {
     using R = typename Real<S>::type;
-    double dmax[4] = {0, 0, 0, 0}, amax[4] = {0, 0, 0, 0}, bad = 0;
+    R dmax[4] = {0, 0, 0, 0}, amax[4] = {0, 0, 0, 0};
+    int bad = 0;
     const size_t n = (size_t)G.nx * G.ny;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(k / G.nx), i = (int)(k - (size_t)j * G.nx);
-        R f[9], g[5], h[5];
-        gather<true>(mode, buf, G, i, j, c, f, g, h);
-        Coef<R> cl = c;
-        if (c.poro) porous_at(cl, (size_t)j * G.pitch + i, G.plane);
-        Macro<R> M = macro(cl, f, g, h);
-        const double phi[4] = {(double)M.ux, (double)M.uy, (double)c.T0 + (double)M.Tp,
-                               (double)c.C0 + (double)M.Cp};
+    const int ntx = (G.nx + RES_THREADS - 1) / RES_THREADS;
+    for (int tx = blockIdx.x; tx < ntx; tx += gridDim.x) {
+        const int i = tx * RES_THREADS + threadIdx.x;
+        if (i >= G.nx) continue;
+        for (int j = blockIdx.y; j < G.ny; j += gridDim.y) {
+            // all loads first (the snapshot's with the populations), then the stores:
+            // a load after a store to the same array waits for nothing, but the
+            // compiler keeps them in program order, which would serialise four
+            // round trips to memory per node
+            const size_t k = (size_t)j * G.nx + i;
+            R old[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const double old = snap[q * n + k];
-            if (!isfinite(phi[q])) bad = 1;
-            dmax[q] = fmax(dmax[q], fabs(phi[q] - old));
-            amax[q] = fmax(amax[q], fabs(phi[q]));
-            snap[q * n + k] = phi[q];
+            for (int q = 0; q < 4; ++q) old[q] = (R)snap[q * n + k];
+            R f[9], g[5], h[5];
+            gather_m<MODE>(buf, G, i, j, c, f, g, h);
+            Macro<R> M;
+            if (EXT && c.poro) {
+                Coef<R> cl = c;
+                porous_at(cl, (size_t)j * G.pitch + i, G.plane);
+                M = macro(cl, f, g, h);
+            } else {
+                M = macro(c, f, g, h);
+            }
+            const R phi[4] = {M.ux, M.uy, M.Tp, M.Cp};
+            const R absv[4] = {M.ux, M.uy, c.T0 + M.Tp, c.C0 + M.Cp};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!finite_(phi[q])) bad = 1;
+                dmax[q] = max_(dmax[q], abs_(phi[q] - old[q]));
+                amax[q] = max_(amax[q], abs_(absv[q]));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) snap[q * n + k] = (P)phi[q];
         }
     }
-    __shared__ double red[RES_THREADS / 32][9];
+    // block maxima in R, one FP64 value per quantity for the slot
+    __shared__ R red[RES_THREADS / 32][9];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double v[9] = {dmax[0], dmax[1], dmax[2], dmax[3], amax[0], amax[1], amax[2], amax[3], bad};
+    const R v[9] = {dmax[0], dmax[1], dmax[2], dmax[3], amax[0], amax[1], amax[2], amax[3], (R)bad};
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        const double r = warp_max(v[q]);
+        const R r = warp_max(v[q]);
         if (lane == 0) red[warp][q] = r;
     }
     __syncthreads();
     if (threadIdx.x < 9) {
-        double s = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w][threadIdx.x]);
-        partial[(size_t)blockIdx.x * 9 + threadIdx.x] = s;
+        R s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = max_(s, red[w][threadIdx.x]);
+        const size_t b = ((size_t)blockIdx.y * gridDim.x + blockIdx.x) % (size_t)nslots;
+        atomicMax(slots + b * 9 + threadIdx.x, (unsigned long long)__double_as_longlong((double)s));
     }
+}
+
+// Clears the slots and launches pass 1 with the gather mode and the porous-field
+// code fixed at compile time.
+template <typename S, typename P>
+cudaError_t launch_residual_pass1(const S* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
+                                  int mode, P* snap, double* slots, int nslots, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(slots, 0, (size_t)nslots * 9 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid = residual_grid(G);
+    unsigned long long* sl = reinterpret_cast<unsigned long long*>(slots);
+#define LBM_RES_CASE(M)                                                                          \
+    if (mode == M) {                                                                             \
+        if (c.poro)                                                                              \
+            residual_kernel<S, true, P, M><<<grid, RES_THREADS, 0, st>>>(buf, G, c, snap, sl,     \
+                                                                        nslots);                 \
+        else                                                                                     \
+            residual_kernel<S, false, P, M><<<grid, RES_THREADS, 0, st>>>(buf, G, c, snap, sl,    \
+                                                                         nslots);                \
+        return cudaGetLastError();                                                               \
+    }
+    LBM_RES_CASE(GATHER_PULL_AB)
+    LBM_RES_CASE(GATHER_PULL_AA)
+    LBM_RES_CASE(GATHER_LOCAL)
+#undef LBM_RES_CASE
+    return cudaErrorInvalidValue;
 }
 
 // Residual pass 2: one block folds partial[nblocks][9] into out[9].

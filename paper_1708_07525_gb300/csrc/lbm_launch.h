@@ -63,12 +63,22 @@ cudaError_t launch_nush(const void* buf, const Geom& G, const Coef<typename Real
 template <typename S>
 cudaError_t launch_nush_tb(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
                            int mode, const WallSpec& W, double* out, cudaStream_t st);
-// partial must hold residual_blocks(G) * 9 doubles; out 9 doubles.
+// snap holds 4 * nx * ny values of the compute precision (FP64 for FP64 storage,
+// else FP32); partial must hold RES_SLOTS * 9 doubles; out 9 doubles.
 template <typename S>
 cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
-                            int mode, double* snap, double* partial, double* out,
+                            int mode, void* snap, double* partial, double* out,
                             cudaStream_t st);
-int residual_blocks(const Geom& G);
+// Grid of the residual's first pass: 256-column tiles along x, one row per block
+// along y (each block loops when ny exceeds the grid's y limit).
+inline dim3 residual_grid(const Geom& G) {
+    const int ntx = (G.nx + RES_THREADS - 1) / RES_THREADS;
+    const int gy = G.ny < 65535 ? G.ny : 65535;
+    return dim3((unsigned)ntx, (unsigned)(gy > 0 ? gy : 1), 1);
+}
+// Slots the first pass folds its block maxima into (atomically); the second pass
+// reduces the slots.
+constexpr int RES_SLOTS = 4096;
 
 // Kernel constants of a cavity from its lattice parameters (lbm_api.cu);
 // stochastic rounding of 16-bit stores is enabled (Coef::sr = 1).

@@ -75,13 +75,13 @@ cudaError_t launch_nush_tb(const void* buf, const Geom& G, const Coef<typename R
 
 template <typename S>
 cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
-                            int mode, double* snap, double* partial, double* out,
+                            int mode, void* snap, double* partial, double* out,
                             cudaStream_t st) {
-    const int nb = residual_blocks(G);
-    residual_kernel<S><<<nb, RES_THREADS, 0, st>>>((const S*)buf, G, c, mode, snap, partial);
-    cudaError_t e = cudaGetLastError();
+    using R = typename Real<S>::type;
+    cudaError_t e = launch_residual_pass1<S, R>((const S*)buf, G, c, mode, (R*)snap, partial,
+                                                RES_SLOTS, st);
     if (e != cudaSuccess) return e;
-    residual_final_kernel<<<1, RES_THREADS, 0, st>>>(partial, nb, out);
+    residual_final_kernel<<<1, RES_THREADS, 0, st>>>(partial, RES_SLOTS, out);
     return cudaGetLastError();
 }
 
@@ -102,7 +102,7 @@ cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename 
     template cudaError_t launch_nush_tb<S>(const void*, const Geom&, const Coef<Real<S>::type>&,\
                                            int, const WallSpec&, double*, cudaStream_t);       \
     template cudaError_t launch_residual<S>(const void*, const Geom&,                          \
-                                            const Coef<Real<S>::type>&, int, double*, double*, \
+                                            const Coef<Real<S>::type>&, int, void*, double*,   \
                                             double*, cudaStream_t);
 
 }  // namespace lbm

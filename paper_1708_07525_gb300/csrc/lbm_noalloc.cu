@@ -20,8 +20,6 @@ using namespace lbm;
 
 namespace {
 
-constexpr int NOALLOC_THREADS = RES_THREADS;       // threads per block
-constexpr int NOALLOC_NODES_PER_BLOCK = 4 * RES_THREADS;
 constexpr int NOALLOC_OUT = LBM_NOALLOC_MAX_BLOCKS * 9;   // offset of the 9 results
 
 // Partial maxima of up to LBM_NOALLOC_MAX_BLOCKS blocks (9 doubles each) plus the
@@ -59,14 +57,14 @@ inline const Coef<double>& coef_of(const CtxView& v, double*) { return *v.cd; }
 inline const Coef<float>& coef_of(const CtxView& v, float*) { return *v.cf; }
 
 template <typename S>
-cudaError_t launch(const CtxView& v, double* snap, double* scratch, int nb) {
+cudaError_t launch(const CtxView& v, double* snap, double* scratch) {
     using R = typename Real<S>::type;
     const Coef<R>& c = coef_of(v, (R*)nullptr);
-    residual_kernel<S><<<nb, NOALLOC_THREADS, 0, v.stream>>>((const S*)v.buf, v.G, c, v.mode, snap,
-                                                             scratch);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_residual_pass1<S, double>((const S*)v.buf, v.G, c, v.mode, snap, scratch,
+                                                     LBM_NOALLOC_MAX_BLOCKS, v.stream);
     if (e != cudaSuccess) return e;
-    residual_final_kernel<<<1, RES_THREADS, 0, v.stream>>>(scratch, nb, scratch + NOALLOC_OUT);
+    residual_final_kernel<<<1, RES_THREADS, 0, v.stream>>>(scratch, LBM_NOALLOC_MAX_BLOCKS,
+                                                          scratch + NOALLOC_OUT);
     return cudaGetLastError();
 }
 
@@ -85,23 +83,16 @@ lbm_status lbm_residual_noalloc(lbm_ctx* ctx, double* snapshot, int have_snapsho
     CtxView v;
     if (!ctx || !snapshot || !r || !lbm_ctx_view(ctx, &v))
         return fail(ctx, LBM_ERR_INVALID, "ctx, snapshot and r must be non-NULL");
-    const size_t n = (size_t)v.G.nx * v.G.ny;
-    if (n > (size_t)LBM_NOALLOC_MAX_NODES) {
-        char d[128];
-        std::snprintf(d, sizeof d, " (grid of %zu nodes; the limit is %d)", n, LBM_NOALLOC_MAX_NODES);
-        return fail(ctx, LBM_ERR_INVALID, "grid larger than the static scratch supports", d);
-    }
-    const int nb = (int)((n + NOALLOC_NODES_PER_BLOCK - 1) / NOALLOC_NODES_PER_BLOCK);
     double* scratch = nullptr;
     cudaError_t e = scratch_for_device(v.device, &scratch);
     if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, "cudaGetSymbolAddress: ", cudaGetErrorString(e));
-    // Every partial slot the fold reads is written by this call, and the fold writes all
-    // nine results, so nothing in the shared array has to be cleared first.
+    // The call clears the slots of the shared array before its first pass folds into
+    // them, and the fold writes all nine results.
     switch (v.prec) {
-        case LBM_F64: e = launch<double>(v, snapshot, scratch, nb); break;
-        case LBM_F32: e = launch<float>(v, snapshot, scratch, nb); break;
-        case LBM_BF16: e = launch<__nv_bfloat16>(v, snapshot, scratch, nb); break;
-        default: e = launch<__half>(v, snapshot, scratch, nb); break;
+        case LBM_F64: e = launch<double>(v, snapshot, scratch); break;
+        case LBM_F32: e = launch<float>(v, snapshot, scratch); break;
+        case LBM_BF16: e = launch<__nv_bfloat16>(v, snapshot, scratch); break;
+        default: e = launch<__half>(v, snapshot, scratch); break;
     }
     double h[9];
     if (e == cudaSuccess)

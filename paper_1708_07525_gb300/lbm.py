@@ -20,7 +20,6 @@ AB_PULL, AA = 0, 1
 WALL_DIRICHLET, WALL_ADIABATIC = 0, 1
 PRECISIONS = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
 LAYOUTS = {"ab": AB_PULL, "aa": AA}
-NOALLOC_MAX_NODES = 4096 * 1024   # LBM_NOALLOC_MAX_NODES
 
 OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_UNCONVERGED = range(7)
 _STATUS = {1: "LBM_ERR_INVALID", 2: "LBM_ERR_NOMEM", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_DIVERGED",
