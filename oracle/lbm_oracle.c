@@ -97,12 +97,15 @@ static void ensure_inverses(void)
 int or_derive(or_params* p)
 {
     if (p->nx < 3 || p->ny < 3) return 1;
+    if (p->nee && (p->nx < 5 || p->ny < 5)) return 1;   /* x_ff must be an interior node */
     if (!(p->eps > 0.0 && p->eps <= 1.0) || !(p->Da > 0.0) || !(p->Ra > 0.0) || !(p->Pr > 0.0) ||
         !(p->Le > 0.0) || !(p->J > 0.0) || !(p->sigma > 0.0))
         return 1;
     if (p->Ma <= 0.0) p->Ma = 0.1;          /* Sec. 4.1: Ma = 0.1 */
     if (p->varpi <= 0.0) p->varpi = 0.4;    /* Sec. 4: varpi = 2/5 */
-    double L = (double)p->nx;               /* Sec. 4.1: L = N_x in lattice units */
+    /* Sec. 4.1: L = N_x in lattice units; with nodes on the walls the N_x lattice
+     * spacings between the walls take N_x + 1 nodes */
+    double L = p->nee ? (double)(p->nx - 1) : (double)p->nx;
     p->rho0 = 1.0;
     p->cs2 = 1.0 / 3.0;                     /* c_s = c / sqrt(3) */
     p->U = p->Ma * sqrt(p->cs2);            /* Ma = U / c_s */
@@ -135,6 +138,8 @@ int or_derive(or_params* p)
     p->Tw[0] = 1.0; p->Tw[1] = 0.0; p->Tw[2] = 0.5; p->Tw[3] = 0.5;
     p->Cw[0] = 1.0; p->Cw[1] = 0.0; p->Cw[2] = 0.5; p->Cw[3] = 0.5;
     memset(p->uw, 0, sizeof p->uw);
+    memset(p->BiT, 0, sizeof p->BiT);
+    memset(p->BiC, 0, sizeof p->BiC);
     p->Gx = 0.0;
     p->model_a = 0;
     for (int k = 0; k < 9; ++k) if (!(p->s[k] > 0.0 && p->s[k] < 2.0)) return 2;
@@ -225,6 +230,35 @@ static void macro(const or_params* p, const double f[9], const double g[5], cons
     o->ux = ux; o->uy = uy; o->Fx = Fx; o->Fy = Fy;
 }
 
+/* Eq. 14 with alpha_1 = 1, alpha_2 = -3 (Sec. 3.1): equilibrium moments of f. */
+static void meq9(const or_params* p, double rho, double ux, double uy, double meq[9])
+{
+    double rho0 = p->rho0, eps = p->eps;
+    double u2 = ux * ux + uy * uy;
+    double a1 = 1.0, a2 = -3.0;
+    meq[0] = rho;
+    meq[1] = -2.0 * rho + 3.0 * rho0 * u2 / eps;
+    meq[2] = a1 * rho + a2 * rho0 * u2 / eps;
+    meq[3] = rho0 * ux;
+    meq[4] = -rho0 * ux;
+    meq[5] = rho0 * uy;
+    meq[6] = -rho0 * uy;
+    meq[7] = rho0 * (ux * ux - uy * uy) / eps;
+    meq[8] = rho0 * ux * uy / eps;
+}
+
+/* Eqs. 24/25 (model A: Eqs. 30/31): equilibrium moments of the D2Q5 lattice of a
+ * scalar Phi whose zeroth moment carries the factor cap (sigma for T, eps for C). */
+static void neq5(const or_params* p, double cap, double Phi, double ux, double uy, double neq[5])
+{
+    double varpi = p->varpi;
+    neq[0] = cap * Phi;
+    neq[1] = ux * Phi;
+    neq[2] = uy * Phi;
+    neq[3] = p->model_a ? (-4.0 + 5.0 * varpi) * cap * Phi : -4.0 * cap * Phi + 5.0 * varpi * Phi;
+    neq[4] = 0.0;
+}
+
 /* D2Q5 collision (Eqs. 21/22 with Eqs. 24/25 and 27) for a scalar Phi whose
  * zeroth moment carries the factor `cap` (sigma for T, eps for C). */
 static void collide_d2q5(const or_params* p, const double rates[5], double cap, double Phi,
@@ -247,8 +281,8 @@ static void collide_d2q5(const or_params* p, const double rates[5], double cap, 
         for (int i = 0; i < 5; ++i) n[k] += N5[k][i] * d[i];
     }
     /* Eqs. 24/25: modified equilibrium moments; model A: Eqs. 30/31 */
-    double neq[5] = {cap * Phi, ux * Phi, uy * Phi, -4.0 * cap * Phi + 5.0 * varpi * Phi, 0.0};
-    if (p->model_a) neq[3] = (-4.0 + 5.0 * varpi) * cap * Phi;
+    double neq[5];
+    neq5(p, cap, Phi, ux, uy, neq);
     /* n* = n - Theta (n - n_eq) + (I - Theta/2) S */
     double ns[5];
     for (int k = 0; k < 5; ++k)
@@ -271,18 +305,9 @@ static void collide(const or_params* p, const double f[9], const double g[5], co
         m[k] = 0;
         for (int i = 0; i < 9; ++i) m[k] += M9[k][i] * f[i];
     }
-    /* Eq. 14 with alpha_1 = 1, alpha_2 = -3 (Sec. 3.1) */
-    double u2 = ux * ux + uy * uy;
-    double a1 = 1.0, a2 = -3.0;
-    double meq[9] = {rho,
-                     -2.0 * rho + 3.0 * rho0 * u2 / eps,
-                     a1 * rho + a2 * rho0 * u2 / eps,
-                     rho0 * ux,
-                     -rho0 * ux,
-                     rho0 * uy,
-                     -rho0 * uy,
-                     rho0 * (ux * ux - uy * uy) / eps,
-                     rho0 * ux * uy / eps};
+    /* Eq. 14 */
+    double meq[9];
+    meq9(p, rho, ux, uy, meq);
     /* Eq. 15 */
     double uF = ux * Fx + uy * Fy;
     double S[9] = {0.0,
@@ -321,6 +346,109 @@ void or_collide_node(const or_params* p, const double f[9], const double g[5],
     collide(p, f, g, h, hist, fs, gs, hs, &o);
     mac[0] = o.rho; mac[1] = o.ux; mac[2] = o.uy; mac[3] = o.T; mac[4] = o.C;
     mac[5] = o.Fx; mac[6] = o.Fy;
+}
+
+/* ---- walls with nodes on them (Sec. 3.3) -------------------------------------------- */
+
+/* Value of the scalar Phi (T or C) at a boundary node whose inward link to the
+ * nearest interior node is (di, dj), from Phi_f at x_f = x_b + (di, dj) and Phi_ff
+ * at x_ff = x_b + 2 (di, dj).  A Dirichlet wall at the node gives its value (the
+ * left / right wall first at a corner).  Otherwise every wall at the node is of
+ * gradient type and Eq. 36/37 applies along (di, dj):
+ *   Phi_b = (4 Phi_f - Phi_ff - 2 dx . grad Phi_b) / 3,
+ * where each wall contributes its inward derivative, dx . grad Phi = sum over the
+ * walls of (Bi / L)(Phi_b - Phi_w) (Eq. 39 as a convective condition, Bi = 0 for
+ * an adiabatic wall); solved for Phi_b. */
+static double nee_scalar(const or_params* p, int di, int dj, const double W[4], const double Bi[4],
+                         double Phi_f, double Phi_ff)
+{
+    const double L = (double)(p->nx - 1);
+    int sides[2], ns = 0;
+    if (di) sides[ns++] = di > 0 ? 0 : 1;
+    if (dj) sides[ns++] = dj > 0 ? 2 : 3;
+    for (int k = 0; k < ns; ++k) {
+        int sd = sides[k];
+        int kind = sd < 2 ? p->scalar_lr : p->scalar_tb;
+        if (!(Bi[sd] > 0.0) && kind == OR_DIRICHLET) return W[sd];
+    }
+    double a = 0.0, b = 0.0;   /* sum of Bi / L and of (Bi / L) Phi_w */
+    for (int k = 0; k < ns; ++k) {
+        int sd = sides[k];
+        if (Bi[sd] > 0.0) {
+            a += Bi[sd] / L;
+            b += Bi[sd] / L * W[sd];
+        }
+    }
+    return (4.0 * Phi_f - Phi_ff + 2.0 * b) / (3.0 + 2.0 * a);
+}
+
+/* Eqs. 33-35 at every boundary node of the arrays F, G, H (layout [q][ny][nx]),
+ * from the post-streaming values at interior nodes.  x_f is the nearest interior
+ * node along the inward wall normal (the diagonal one at a corner), x_ff the next
+ * one along the same link.  The full sets f, g, h of the boundary node are
+ * replaced:
+ *   f_i(x_b) = f_i^eq(rho(x_f), u_w) + f_i(x_f) - f_i^eq(rho(x_f), u(x_f))     (Eq. 33)
+ *   g_i(x_b) = g_i^eq(T_b, u_w) + g_i(x_f) - g_i^eq(T(x_f), u(x_f))            (Eq. 34)
+ *   h_i(x_b) = h_i^eq(C_b, u_w) + h_i(x_f) - h_i^eq(C(x_f), u(x_f))            (Eq. 35)
+ * with the equilibria f^eq = M^-1 m^eq (Eq. 14) and g^eq = N^-1 n^eq (Eqs. 24/25),
+ * each at its own node's porosity, u(x_f) from Eq. 18, T_b / C_b from the wall's
+ * Dirichlet value or Eqs. 36/37, and u_w the velocity of the wall (the bottom /
+ * top wall's at a corner).  Only interior nodes are read, so the order of the
+ * boundary nodes does not matter. */
+static void nee_apply(const or_state* s, double* F, double* G, double* H)
+{
+    const or_params* p = &s->p;
+    const int nx = p->nx, ny = p->ny;
+    const size_t n = s->n;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int di = 0, dj = 0;
+            if (!p->periodic_x) di = i == 0 ? 1 : (i == nx - 1 ? -1 : 0);
+            if (!p->periodic_y) dj = j == 0 ? 1 : (j == ny - 1 ? -1 : 0);
+            if (!di && !dj) continue;
+            const size_t xb = (size_t)j * nx + i;
+            const size_t xf = (size_t)(j + dj) * nx + (i + di);
+            const size_t xff = (size_t)(j + 2 * dj) * nx + (i + 2 * di);
+            double ff[9], gf[5], hf[5];
+            for (int q = 0; q < 9; ++q) ff[q] = F[q * n + xf];
+            for (int q = 0; q < 5; ++q) { gf[q] = G[q * n + xf]; hf[q] = H[q * n + xf]; }
+            const or_params pb = node_params(s, xb), pf = node_params(s, xf), pff = node_params(s, xff);
+            or_macro of;
+            macro(&pf, ff, gf, hf, &of);
+            double sgff = 0, shff = 0;
+            for (int q = 0; q < 5; ++q) { sgff += G[q * n + xff]; shff += H[q * n + xff]; }
+            const double Tff = sgff / pff.sigma, Cff = shff / pff.eps;   /* Eq. 26 */
+            const int sv = dj ? (dj > 0 ? 2 : 3) : (di > 0 ? 0 : 1);
+            const double uwx = p->uw[sv][0], uwy = p->uw[sv][1];
+            /* Eq. 33 */
+            double mb[9], mf[9];
+            meq9(&pb, of.rho, uwx, uwy, mb);
+            meq9(&pf, of.rho, of.ux, of.uy, mf);
+            for (int q = 0; q < 9; ++q) {
+                double eb = 0, ef = 0;
+                for (int k = 0; k < 9; ++k) { eb += M9inv[q][k] * mb[k]; ef += M9inv[q][k] * mf[k]; }
+                F[q * n + xb] = eb + ff[q] - ef;
+            }
+            /* Eqs. 34-37 */
+            const double Tb = nee_scalar(p, di, dj, p->Tw, p->BiT, of.T, Tff);
+            const double Cb = nee_scalar(p, di, dj, p->Cw, p->BiC, of.C, Cff);
+            double nb[5], nf[5], kb[5], kf[5];
+            neq5(&pb, pb.sigma, Tb, uwx, uwy, nb);
+            neq5(&pf, pf.sigma, of.T, of.ux, of.uy, nf);
+            neq5(&pb, pb.eps, Cb, uwx, uwy, kb);
+            neq5(&pf, pf.eps, of.C, of.ux, of.uy, kf);
+            for (int q = 0; q < 5; ++q) {
+                double gb = 0, gff = 0, hb = 0, hff = 0;
+                for (int k = 0; k < 5; ++k) {
+                    gb += N5inv[q][k] * nb[k];
+                    gff += N5inv[q][k] * nf[k];
+                    hb += N5inv[q][k] * kb[k];
+                    hff += N5inv[q][k] * kf[k];
+                }
+                G[q * n + xb] = gb + gf[q] - gff;
+                H[q * n + xb] = hb + hf[q] - hff;
+            }
+        }
 }
 
 /* ---- creation ---------------------------------------------------------------- */
@@ -390,6 +518,8 @@ or_state* or_create_field(const or_params* p, uint64_t seed, double noise, const
                 }
             }
         }
+    /* with nodes on the walls the state at t = 0 obeys the wall rules too */
+    if (p->nee) nee_apply(s, s->f, s->g, s->h);
     /* history = (T u, C u) of the initial state */
     for (size_t x = 0; x < n; ++x) {
         double fl[9], gl[5], hl[5];
@@ -446,6 +576,8 @@ void or_step(or_state* s, long nsteps)
                     if (p->periodic_y) tj = (tj + ny) % ny;
                     if (ti >= 0 && ti < nx && tj >= 0 && tj < ny) {
                         s->f2[q * n + (size_t)tj * nx + ti] = fs[q];
+                    } else if (p->nee) {
+                        /* leaves through a wall node: the wall rule rebuilds what enters */
                     } else {
                         /* halfway bounce-back off a wall moving with u_w (a resting wall:
                          * no-slip): f_opp(x) = f*_q(x) - 2 w_q rho0 (e_q . u_w) / c_s^2.
@@ -464,6 +596,7 @@ void or_step(or_state* s, long nsteps)
                         s->h2[q * n + (size_t)tj * nx + ti] = hs[q];
                         continue;
                     }
+                    if (p->nee) continue;
                     int lr = (ti < 0 || ti >= nx);           /* left/right wall link */
                     int type = lr ? p->scalar_lr : p->scalar_tb;
                     if (type == OR_DIRICHLET) {
@@ -481,6 +614,8 @@ void or_step(or_state* s, long nsteps)
                 }
             }
         }
+        /* Sec. 3.3: boundary nodes from the post-streaming interior */
+        if (p->nee) nee_apply(s, s->f2, s->g2, s->h2);
         double* t;
         t = s->f; s->f = s->f2; s->f2 = t;
         t = s->g; s->g = s->g2; s->g2 = t;
@@ -523,6 +658,25 @@ void or_nusselt_sherwood(const or_state* s, double out[4])
     or_fields(s, NULL, NULL, T, C, NULL);
     double dT = p->Tw[0] - p->Tw[1], dC = p->Cw[0] - p->Cw[1];
     double nuL = 0, shL = 0, nuR = 0, shR = 0;
+    if (p->nee) {
+        /* nodes on the walls: dPhi/dx|wall = (-3 Phi_0 + 4 Phi_1 - Phi_2) / 2 (left),
+         * mirrored on the right; L = nx - 1; trapezoidal mean over y in [0, ny - 1] */
+        const double L = (double)(nx - 1);
+        for (int j = 0; j < ny; ++j) {
+            const double* Tr = T + (size_t)j * nx;
+            const double* Cr = C + (size_t)j * nx;
+            const double wj = (j == 0 || j == ny - 1) ? 0.5 : 1.0;
+            nuL += wj * -L * (-3.0 * Tr[0] + 4.0 * Tr[1] - Tr[2]) / 2.0 / dT;
+            shL += wj * -L * (-3.0 * Cr[0] + 4.0 * Cr[1] - Cr[2]) / 2.0 / dC;
+            nuR += wj * -L * (3.0 * Tr[nx - 1] - 4.0 * Tr[nx - 2] + Tr[nx - 3]) / 2.0 / dT;
+            shR += wj * -L * (3.0 * Cr[nx - 1] - 4.0 * Cr[nx - 2] + Cr[nx - 3]) / 2.0 / dC;
+        }
+        out[0] = nuL / (ny - 1); out[1] = shL / (ny - 1);
+        out[2] = nuR / (ny - 1); out[3] = shR / (ny - 1);
+        free(T);
+        free(C);
+        return;
+    }
     for (int j = 0; j < ny; ++j) {
         const double* Tr = T + (size_t)j * nx;
         const double* Cr = C + (size_t)j * nx;
@@ -550,6 +704,25 @@ void or_nusselt_sherwood_tb(const or_state* s, double out[4])
     or_fields(s, NULL, NULL, T, C, NULL);
     double dT = p->Tw[3] - p->Tw[2], dC = p->Cw[3] - p->Cw[2];
     double nuB = 0, shB = 0, nuT = 0, shT = 0;
+    if (p->nee) {
+        /* as the left / right walls, transposed: L = ny - 1, trapezoidal mean over x */
+        const double L = (double)(ny - 1);
+        for (int i = 0; i < nx; ++i) {
+            const double wi = (i == 0 || i == nx - 1) ? 0.5 : 1.0;
+            const double* t0 = T + i;
+            const double* c0 = C + i;
+            const size_t r = (size_t)nx, top = (size_t)(ny - 1) * nx;
+            nuB += wi * L * (-3.0 * t0[0] + 4.0 * t0[r] - t0[2 * r]) / 2.0 / dT;
+            shB += wi * L * (-3.0 * c0[0] + 4.0 * c0[r] - c0[2 * r]) / 2.0 / dC;
+            nuT += wi * L * (3.0 * t0[top] - 4.0 * t0[top - r] + t0[top - 2 * r]) / 2.0 / dT;
+            shT += wi * L * (3.0 * c0[top] - 4.0 * c0[top - r] + c0[top - 2 * r]) / 2.0 / dC;
+        }
+        out[0] = nuB / (nx - 1); out[1] = shB / (nx - 1);
+        out[2] = nuT / (nx - 1); out[3] = shT / (nx - 1);
+        free(T);
+        free(C);
+        return;
+    }
     for (int i = 0; i < nx; ++i) {
         double T0 = T[i], T1 = T[(size_t)nx + i];
         double C0 = C[i], C1 = C[(size_t)nx + i];
@@ -563,6 +736,25 @@ void or_nusselt_sherwood_tb(const or_state* s, double out[4])
     out[0] = nuB / nx; out[1] = shB / nx; out[2] = nuT / nx; out[3] = shT / nx;
     free(T);
     free(C);
+}
+
+void or_stream_function(const or_state* s, double* psi)
+{
+    const or_params* p = &s->p;
+    const int nx = p->nx, ny = p->ny;
+    double* ux = (double*)malloc(s->n * sizeof(double));
+    or_fields(s, ux, NULL, NULL, NULL, NULL);
+    for (int i = 0; i < nx; ++i) {
+        /* from the wall node (psi = 0), or from the halfway wall at distance 1/2 below
+         * node 0 where u = 0: the trapezoid over that half spacing is u_0 / 4 */
+        double acc = p->nee ? 0.0 : 0.25 * ux[i];
+        psi[i] = acc;
+        for (int j = 1; j < ny; ++j) {
+            acc += 0.5 * (ux[(size_t)(j - 1) * nx + i] + ux[(size_t)j * nx + i]);
+            psi[(size_t)j * nx + i] = acc;
+        }
+    }
+    free(ux);
 }
 
 void or_get(const or_state* s, double* f, double* g, double* h, double* hist)

@@ -18,13 +18,27 @@
  *   - optionally the coupled "model A" equilibria (negative
  *     control of Sec. 3.2)                                     Eqs. 30-32
  *   - streaming in velocity space                              Eq. 11
+ *   - optional walls with nodes on them: non-equilibrium
+ *     extrapolation and gradient extrapolation                Sec. 3.3, Eqs. 33-37
+ *   - convective (Robin) walls                                 Sec. 4.2, Eq. 39
  *   - Nusselt / Sherwood numbers                               Sec. 4.1, Eq. 38
  *   - parameter mapping from Ra, Pr, Le, Da, Ma                Sec. 4 and 4.1
  * Readings where the paper is silent (all stated again beside the code):
- *   - walls: no-slip halfway bounce-back for f; anti-bounce-back (Dirichlet)
- *     and bounce-back (adiabatic) for g, h.  The paper itself uses
- *     non-equilibrium extrapolation (Sec. 3.3); the cavity workloads specify
- *     halfway walls.
+ *   - walls (default): no-slip halfway bounce-back for f; anti-bounce-back
+ *     (Dirichlet) and bounce-back (adiabatic) for g, h.  The cavity workloads
+ *     specify halfway walls.
+ *   - walls (nee = 1): the paper's own scheme (Sec. 3.3) with nodes on the
+ *     walls.  Each step streams, then rebuilds the full sets f, g, h of every
+ *     wall node by Eqs. 33-35 from the nearest interior node along the inward
+ *     normal (the diagonal one at a corner); the rebuilt node then collides
+ *     like any other.  Wall T / C: the Dirichlet value, else Eqs. 36-37 along
+ *     the same link, where a convective wall (Eq. 39) enters as
+ *     dPhi/dn = -(Bi / L)(Phi - Phi_ambient) along the outward normal (the sign
+ *     the paper leaves implicit: heat leaves through the wall); at a corner the
+ *     Dirichlet wall wins, else both walls' gradients enter.  The state at
+ *     t = 0 is rebuilt the same way.
+ *   - Robin / convective wall, Eq. 39: Bi = h L / alpha_e with L the cavity
+ *     width nx - 1 on every side.
  *   - the time derivative of T*u in Eq. 27 is the explicit backward
  *     difference the paper suggests (Sec. 3.2), with the history initialised
  *     to T*u of the initial state, so the source vanishes at the first step.
@@ -32,7 +46,9 @@
  *
  * Parity status: every function here is pinned by tests under tests/
  * (identities between the paper's moment- and velocity-space forms,
- * conservation, exact conduction profile, Brinkman channel, Table 1).
+ * conservation, exact conduction profiles, Brinkman channels, Tables 1-4;
+ * for nee: exact Dirichlet and convective conduction profiles, the channel's
+ * second-order convergence, Sec. 3.2's T = C at Le = 1 and Tables 2-3).
  */
 #ifndef LBM_ORACLE_H
 #define LBM_ORACLE_H
@@ -63,11 +79,20 @@ typedef struct {
     double Gx;                  /* constant external body force along x (enters as eps*G) */
     int model_a;                /* 1: the coupled equilibria of Eqs. 30-31 ("model A"), whose
                                    diffusivities follow Eq. 32; 0: Eqs. 24-25 (the paper's model) */
+    int nee;                    /* 0: halfway walls (half a spacing outside the outermost nodes);
+                                   1: the outermost nodes lie on the walls, which follow the
+                                   non-equilibrium extrapolation of Sec. 3.3 (Eqs. 33-37); the
+                                   cavity width is then L = nx - 1 (an input of or_derive) */
+    double BiT[4], BiC[4];      /* nee only: a side with Bi > 0 is a convective (Robin) wall,
+                                   Eq. 39: dPhi/dn = -(Bi / L) (Phi - Phi_w) along the outward
+                                   normal n, Phi_w = Tw / Cw of that side the ambient value;
+                                   Bi = 0 keeps the side's Dirichlet / adiabatic kind */
 } or_params;
 
 typedef struct or_state or_state;
 
-/* Fill the derived fields of p from nx, Ra, Da, eps, Pr, Le, N, J, sigma, Ma, varpi.
+/* Fill the derived fields of p from nx, Ra, Da, eps, Pr, Le, N, J, sigma, Ma, varpi
+ * and nee (L = nx, or nx - 1 when nee).  The wall knobs are reset (BiT = BiC = 0).
  * Returns 0 on success, nonzero if a relaxation rate leaves (0,2) or an input is invalid. */
 int or_derive(or_params* p);
 
@@ -92,11 +117,17 @@ long or_time(const or_state* s);
  * Any pointer may be NULL. u is from Eq. 18, T and C from Eq. 26, rho from Eq. 16. */
 void or_fields(const or_state* s, double* ux, double* uy, double* T, double* C, double* rho);
 
-/* Mean Nu and Sh on the left and right walls (Eq. 38), out = {Nu_L, Sh_L, Nu_R, Sh_R}. */
+/* Mean Nu and Sh on the left and right walls (Eq. 38), out = {Nu_L, Sh_L, Nu_R, Sh_R};
+ * dT = Tw[0] - Tw[1] (hot wall minus cold wall, or minus the ambient of a convective wall). */
 void or_nusselt_sherwood(const or_state* s, double out[4]);
 /* Mean Nu and Sh on the bottom and top walls, out = {Nu_B, Sh_B, Nu_T, Sh_T}: the wall-normal
  * gradient times L = ny over (Phi_top - Phi_bottom), averaged over the nx columns. */
 void or_nusselt_sherwood_tb(const or_state* s, double out[4]);
+
+/* Stream function psi[ny][nx] with u_x = d psi / dy, psi = 0 on the bottom wall:
+ * the trapezoidal rule up each column (from the wall node when nee, else from the
+ * halfway wall half a spacing below the first node, where u = 0). */
+void or_stream_function(const or_state* s, double* psi);
 
 /* Copy the distributions out / in, layout [q][ny][nx]; hist is [4][ny][nx] =
  * (T u_x, T u_y, C u_x, C u_y) at the previous collision. */

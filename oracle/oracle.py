@@ -46,6 +46,8 @@ class Params(C.Structure):
         ("uw", (C.c_double * 2) * 4),
         ("Gx", C.c_double),
         ("model_a", C.c_int),
+        ("nee", C.c_int),
+        ("BiT", C.c_double * 4), ("BiC", C.c_double * 4),
     ]
 
 
@@ -82,6 +84,7 @@ def lib():
             L.or_fields.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
             L.or_nusselt_sherwood.argtypes = [C.c_void_p, dp]
             L.or_nusselt_sherwood_tb.argtypes = [C.c_void_p, dp]
+            L.or_stream_function.argtypes = [C.c_void_p, dp]
             L.or_get.argtypes = [C.c_void_p, dp, dp, dp, dp]
             L.or_set.argtypes = [C.c_void_p, dp, dp, dp, dp]
             L.or_collide_node.argtypes = [P, dp, dp, dp, dp, dp, dp, dp, dp]
@@ -100,10 +103,13 @@ def _ptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def derive(nx, ny, Ra, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, Ma=0.1, varpi=0.4) -> Params:
-    """Parameter mapping of Sec. 4 / 4.1 (see or_derive)."""
+def derive(nx, ny, Ra, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, Ma=0.1, varpi=0.4,
+           nee=False) -> Params:
+    """Parameter mapping of Sec. 4 / 4.1 (see or_derive); nee: nodes on the walls
+    with the non-equilibrium extrapolation of Sec. 3.3 (then L = nx - 1)."""
     p = Params()
     p.nx, p.ny = int(nx), int(ny)
+    p.nee = 1 if nee else 0
     p.Ra, p.Da, p.eps, p.Pr, p.Le, p.N, p.J, p.sigma = Ra, Da, eps, Pr, Le, N, J, sigma
     p.Ma, p.varpi = Ma, varpi
     rc = lib().or_derive(C.byref(p))
@@ -131,6 +137,17 @@ def derive_lid(nx, ny, Re, Gr, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, U0=0.1, var
     for k, v in enumerate((0.5, 0.5, 0.0, 1.0)):
         p.Tw[k] = p.Cw[k] = v
     p.uw[3][0] = U0
+    return p
+
+
+def derive_convective(Nx, Ra, Da, eps, Pr, Le, N, BiT, BiC, J=1.0, sigma=1.0, Ma=0.1,
+                      varpi=0.4) -> Params:
+    """Porous cavity with a freely convective wall (Sec. 4.2): Nx lattice spacings
+    per side (Nx + 1 nodes on walls), left wall T = C = 1, right wall convective
+    (Eq. 39) to the ambient T = C = 0 with Biot numbers BiT, BiC, top and bottom
+    adiabatic and impermeable; T0 = C0 = 1/2, dT = dC = 1."""
+    p = derive(Nx + 1, Nx + 1, Ra, Da, eps, Pr, Le, N, J, sigma, Ma, varpi, nee=True)
+    p.BiT[1], p.BiC[1] = BiT, BiC
     return p
 
 
@@ -201,6 +218,11 @@ class Oracle:
         out = np.empty(4)
         lib().or_nusselt_sherwood_tb(self.h, _ptr(out))
         return out
+
+    def stream_function(self) -> np.ndarray:
+        psi = np.empty((self.ny, self.nx))
+        lib().or_stream_function(self.h, _ptr(psi))
+        return psi
 
     def get(self):
         shp = (self.ny, self.nx)
