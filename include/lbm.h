@@ -127,6 +127,22 @@ typedef struct {
     int model_a;                /* 0: the paper's equilibria (Eqs. 24-25); 1: the coupled
                                    "model A" equilibria of Eqs. 30-31 (a negative control; with
                                    it, Eq. 32 relates zeta, eta to the diffusivities) */
+    int nee;                    /* 0: halfway walls half a spacing outside the outermost nodes
+                                   (the rules of wall_lr / wall_tb / uw above); 1: the outermost
+                                   nodes lie on the walls and follow the paper's own scheme
+                                   (Sec. 3.3): after streaming, each wall node's f, g, h are
+                                   rebuilt by the non-equilibrium extrapolation of Eqs. 33-35
+                                   from the nearest interior node along the inward normal (the
+                                   diagonal one at a corner), with the wall velocity uw, and T / C
+                                   from the Dirichlet value or the gradient extrapolation of
+                                   Eqs. 36-37.  The cavity width is then L = nx - 1.  Needs
+                                   nx, ny >= 5 and the two-buffer layout. */
+    double BiT[4], BiC[4];      /* nee only: Biot numbers of convective (Robin) walls, Eq. 39.
+                                   A side with Bi > 0 takes dPhi/dn = -(Bi / L)(Phi - Phi_w)
+                                   along its outward normal n, Phi_w = Tw / Cw of that side as
+                                   the ambient value, L = nx - 1; at a corner a Dirichlet wall
+                                   wins, else both walls' gradients enter Eq. 36 along the
+                                   diagonal.  0: the side keeps its wall_lr / wall_tb kind. */
 } lbm_params;
 
 /* Parameter mapping of Sec. 4 and 4.1 (L = nx, c_s^2 = 1/3, U = Ma c_s,
@@ -139,6 +155,21 @@ typedef struct {
 lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, double Pr,
                              double Le, double N, double J, double sigma, double Ma,
                              double varpi, lbm_params* out);
+
+/* The mapping of lbm_derive_params() for walls with nodes on them (nee = 1):
+ * L = nx - 1 (the nx - 1 spacings between the wall nodes), nx, ny >= 5. */
+lbm_status lbm_derive_params_nee(lbm_grid grid, double Ra, double Da, double eps, double Pr,
+                                 double Le, double N, double J, double sigma, double Ma,
+                                 double varpi, lbm_params* out);
+
+/* The porous cavity with a freely convective wall of Sec. 4.2: Nx lattice spacings
+ * per side ((Nx + 1) x (Nx + 1) nodes on walls, nee = 1), left wall T = C = 1,
+ * right wall convective (Eq. 39) to the ambient T = C = 0 with Biot numbers
+ * BiT, BiC, top and bottom adiabatic and impermeable; other groups as in
+ * lbm_derive_params() with L = Nx. */
+lbm_status lbm_derive_params_convective(int Nx, double Ra, double Da, double eps, double Pr,
+                                        double Le, double N, double BiT, double BiC, double J,
+                                        double sigma, double Ma, double varpi, lbm_params* out);
 
 /* Parameter mapping of the lid-driven porous cavity of Sec. 4.3: top wall moving
  * with U0 along +x, top T = C = 1 and bottom T = C = 0 (Dirichlet), left and right

@@ -91,6 +91,23 @@ Coef<R> make_coef(const lbm_params& P) {
             c.wmom[s][d] = (R)(2.0 * 1.0 * P.uw[s][d] / (1.0 / 3.0));   // 2 rho0 u_w / c_s^2
             if (P.uw[s][d] != 0.0) c.moving = 1;
         }
+    // walls with nodes on them (Sec. 3.3)
+    c.nee = P.nee;
+    const double L = P.nx - 1.0;
+    for (int s = 0; s < 4; ++s) {
+        c.TwP[s] = (R)(P.Tw[s] - P.T0);
+        c.CwP[s] = (R)(P.Cw[s] - P.C0);
+        c.bT[s] = (R)(P.nee ? P.BiT[s] / L : 0.0);
+        c.bC[s] = (R)(P.nee ? P.BiC[s] / L : 0.0);
+        c.uwall[s][0] = (R)P.uw[s][0];
+        c.uwall[s][1] = (R)P.uw[s][1];
+    }
+    const double c3T = P.model_a ? (5.0 * P.varpi - 4.0) * P.sigma : 5.0 * P.varpi - 4.0 * P.sigma;
+    const double c3C = P.model_a ? (5.0 * P.varpi - 4.0) * eps : 5.0 * P.varpi - 4.0 * eps;
+    c.aT0 = (R)((P.sigma - c3T) / 5.0);
+    c.aT1 = (R)(P.sigma / 5.0 + c3T / 20.0);
+    c.aC0 = (R)((eps - c3C) / 5.0);
+    c.aC1 = (R)(eps / 5.0 + c3C / 20.0);
     return c;
 }
 template Coef<float> make_coef<float>(const lbm_params&);
@@ -116,6 +133,15 @@ const char* check_params(const lbm_params& P) {
     if (P.wall_lr != LBM_WALL_DIRICHLET && P.wall_lr != LBM_WALL_ADIABATIC) return "bad wall_lr";
     if (P.wall_tb != LBM_WALL_DIRICHLET && P.wall_tb != LBM_WALL_ADIABATIC) return "bad wall_tb";
     if (P.model_a != 0 && P.model_a != 1) return "model_a must be 0 or 1";
+    if (P.nee != 0 && P.nee != 1) return "nee must be 0 or 1";
+    if (P.nee && (P.nx < 5 || P.ny < 5)) return "walls with nodes on them need nx, ny >= 5";
+    for (int k = 0; k < 4; ++k) {
+        if (!(P.BiT[k] >= 0.0) || !(P.BiC[k] >= 0.0) || !std::isfinite(P.BiT[k]) ||
+            !std::isfinite(P.BiC[k]))
+            return "Biot numbers must be finite and >= 0";
+        if (!P.nee && (P.BiT[k] > 0.0 || P.BiC[k] > 0.0))
+            return "convective (Robin) walls need walls with nodes on them (nee = 1)";
+    }
     if ((double)P.nx * (double)P.ny > 4.0e9) return "grid too large";
     return nullptr;
 }
@@ -196,7 +222,7 @@ struct lbm_ctx {
     size_t hist_bytes() const { return (size_t)4 * G.plane * rsz; }
     size_t nodes() const { return (size_t)G.nx * G.ny; }
     int read_mode() const {
-        if (layout == LBM_AB_PULL) return GATHER_PULL_AB;
+        if (layout == LBM_AB_PULL) return P.nee ? GATHER_NEE_AB : GATHER_PULL_AB;
         return (t & 1) ? GATHER_PULL_AA : GATHER_LOCAL;
     }
 };
@@ -311,9 +337,13 @@ void lbm_set_error(lbm_ctx* c, const char* msg) {
 
 extern "C" {
 
-lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, double Pr,
-                             double Le, double N, double J, double sigma, double Ma,
-                             double varpi, lbm_params* out) {
+namespace {
+
+// The mapping of Sec. 4 / 4.1 for a characteristic length of N_x spacings
+// (L = nx for halfway walls, nx - 1 with nodes on the walls).
+lbm_status derive_core(lbm_grid grid, int nee, double Ra, double Da, double eps, double Pr,
+                       double Le, double N, double J, double sigma, double Ma, double varpi,
+                       lbm_params* out) {
     if (!out) {
         set_global_error("lbm_derive_params: out is NULL");
         return LBM_ERR_INVALID;
@@ -333,7 +363,10 @@ lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, do
     std::memset(&P, 0, sizeof P);
     P.nx = grid.nx;
     P.ny = grid.ny;
-    const double L = grid.nx;                       // characteristic length = N_x (Sec. 4.1)
+    P.nee = nee;
+    // characteristic length = N_x spacings (Sec. 4.1): nx halfway cells, or the nx - 1
+    // spacings between wall nodes
+    const double L = nee ? grid.nx - 1.0 : (double)grid.nx;
     const double cs2 = 1.0 / 3.0, cs = std::sqrt(cs2);
     const double U = Ma * cs;                       // Ma = U / c_s
     const double nu_e = J * U * L * std::sqrt(Pr / Ra);
@@ -372,6 +405,36 @@ lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, do
         return LBM_ERR_INVALID;
     }
     *out = P;
+    return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_derive_params(lbm_grid grid, double Ra, double Da, double eps, double Pr,
+                             double Le, double N, double J, double sigma, double Ma,
+                             double varpi, lbm_params* out) {
+    return derive_core(grid, 0, Ra, Da, eps, Pr, Le, N, J, sigma, Ma, varpi, out);
+}
+
+lbm_status lbm_derive_params_nee(lbm_grid grid, double Ra, double Da, double eps, double Pr,
+                                 double Le, double N, double J, double sigma, double Ma,
+                                 double varpi, lbm_params* out) {
+    return derive_core(grid, 1, Ra, Da, eps, Pr, Le, N, J, sigma, Ma, varpi, out);
+}
+
+lbm_status lbm_derive_params_convective(int Nx, double Ra, double Da, double eps, double Pr,
+                                        double Le, double N, double BiT, double BiC, double J,
+                                        double sigma, double Ma, double varpi, lbm_params* out) {
+    if (!(BiT >= 0.0) || !(BiC >= 0.0) || !std::isfinite(BiT) || !std::isfinite(BiC) || Nx < 4) {
+        set_global_error("lbm_derive_params_convective: need Nx >= 4 and finite Bi >= 0");
+        return LBM_ERR_INVALID;
+    }
+    lbm_grid g;
+    g.nx = g.ny = Nx + 1;
+    lbm_status st = derive_core(g, 1, Ra, Da, eps, Pr, Le, N, J, sigma, Ma, varpi, out);
+    if (st != LBM_OK) return st;
+    out->BiT[1] = BiT;                  // the right wall: ambient T = C = 0 (Tw[1], Cw[1])
+    out->BiC[1] = BiC;
     return LBM_OK;
 }
 
@@ -462,6 +525,10 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
     }
     if ((O.alloc == nullptr) != (O.free == nullptr)) {
         set_global_error("lbm_create: alloc and free hooks must be given together");
+        return LBM_ERR_INVALID;
+    }
+    if (params->nee && O.layout != LBM_AB_PULL) {
+        set_global_error("lbm_create: walls with nodes on them (nee) need the two-buffer layout");
         return LBM_ERR_INVALID;
     }
     if (O.block_x < 0 || O.block_y < 0 || O.block_x * O.block_y > 1024 ||
@@ -742,7 +809,8 @@ lbm_status lbm_nusselt_sherwood(lbm_ctx* c, double out[4]) {
     W.C0 = c->P.C0;
     W.dT = c->P.Tw[0] - c->P.Tw[1];
     W.dC = c->P.Cw[0] - c->P.Cw[1];
-    W.L = c->P.nx;
+    W.nee = c->P.nee;
+    W.L = c->P.nee ? c->P.nx - 1.0 : (double)c->P.nx;
     const int mode = c->read_mode();
     const void* b = cur_buf(c);
     cudaError_t e = LBM_DISPATCH(c, launch_nush<double>(b, c->G, c->cd, mode, W, c->d_out, c->stream),
@@ -775,7 +843,8 @@ lbm_status lbm_nusselt_sherwood_tb(lbm_ctx* c, double out[4]) {
     W.C0 = c->P.C0;
     W.dT = c->P.Tw[3] - c->P.Tw[2];
     W.dC = c->P.Cw[3] - c->P.Cw[2];
-    W.L = c->P.ny;
+    W.nee = c->P.nee;
+    W.L = c->P.nee ? c->P.ny - 1.0 : (double)c->P.ny;
     const int mode = c->read_mode();
     const void* b = cur_buf(c);
     cudaError_t e = LBM_DISPATCH(c, launch_nush_tb<double>(b, c->G, c->cd, mode, W, c->d_out + 20, c->stream),

@@ -143,6 +143,10 @@ bool params_ok(const lbm_params& P, std::string* why) {
     for (int s = 0; s < 4; ++s)
         if (P.uw[s][0] != 0.0 || P.uw[s][1] != 0.0)
             return bad("moving walls are not supported in batches (use a single cavity)");
+    if (P.nee) return bad("walls with nodes on them (nee) are not supported in batches");
+    for (int s = 0; s < 4; ++s)
+        if (P.BiT[s] != 0.0 || P.BiC[s] != 0.0)
+            return bad("convective walls are not supported in batches");
     if (P.nx < 3 || P.ny < 3) return bad("nx and ny must be >= 3");
     if (!(P.eps > 0.0 && P.eps <= 1.0)) return bad("eps must lie in (0, 1]");
     if (!(P.sigma > 0.0) || !(P.K > 0.0)) return bad("sigma and K must be positive");

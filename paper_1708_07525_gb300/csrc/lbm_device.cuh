@@ -151,6 +151,15 @@ struct Coef {
     // the porous constants above are recomputed per node (porous_at).
     const R* poro;
     R nu, varpi5;              // fluid viscosity of Eq. 5, 5 varpi of Eq. 25
+    // Walls with nodes on them (Sec. 3.3, nee = 1): wall values Phi_w - Phi0 by side,
+    // Bi / L of convective sides (Eq. 39; 0 otherwise), wall velocities, and the D2Q5
+    // equilibria as g_eq,0 = a0 Phi, g_eq,i = a1 Phi + (e_i . u) Phi / 2 (i = 1..4) with
+    // a0 = (cap - c3) / 5, a1 = cap / 5 + c3 / 20 (N^-1 n_eq of Eqs. 24-25 / 30-31).
+    int nee;
+    R TwP[4], CwP[4];
+    R bT[4], bC[4];
+    R uwall[4][2];
+    R aT0, aT1, aC0, aC1;
 };
 
 
@@ -186,6 +195,8 @@ __device__ __forceinline__ void porous_at(Coef<R>& c, size_t self, size_t plane)
     c.l0sq = c.l0 * c.l0;
     c.l1 = R(0.5) * c.drag_quad;
     c.c3C = c.varpi5 - R(4) * e;
+    c.aC0 = (e - c.c3C) * R(0.2);
+    c.aC1 = e * R(0.2) + c.c3C * R(0.05);
 }
 
 // Macroscopic quantities of one node from pre-collision deviations.

@@ -96,6 +96,90 @@ __device__ __forceinline__ void gather_local(const S* __restrict__ buf, const Ge
     }
 }
 
+// ---- walls with nodes on them (Sec. 3.3) --------------------------------------------
+// Wall value (deviation) of a scalar at a wall node whose inward link is (di, dj):
+// a Dirichlet side at the node gives its value (the left / right side first);
+// otherwise Eq. 36 / 37 along the link, Phi_b = (4 Phi_f - Phi_ff - 2 dx . grad Phi_b) / 3,
+// with dx . grad Phi_b = sum over the node's sides of b_s (Phi_b - Phi_w,s) (b_s = Bi / L
+// of a convective side, Eq. 39; 0 for an adiabatic one), solved for Phi_b.
+template <typename R>
+__device__ __forceinline__ R nee_scalar(const Coef<R>& c, int di, int dj, const R Pw[4],
+                                        const R b[4], R Pf, R Pff) {
+    const int sv = di > 0 ? 0 : 1, sh = dj > 0 ? 2 : 3;
+    if (di && b[sv] == R(0) && ((c.dirichlet_mask >> sv) & 1)) return Pw[sv];
+    if (dj && b[sh] == R(0) && ((c.dirichlet_mask >> sh) & 1)) return Pw[sh];
+    R a = R(0), w = R(0);
+    if (di) { a += b[sv]; w += b[sv] * Pw[sv]; }
+    if (dj) { a += b[sh]; w += b[sh] * Pw[sh]; }
+    return (R(4) * Pf - Pff + R(2) * w) / (R(3) + R(2) * a);
+}
+
+// Pre-collision populations (deviations) of wall node (i, j) with inward link (di, dj)
+// in the two-buffer pull layout, rebuilt by Eqs. 33-35 from the nearest interior node
+// x_f = (i + di, j + dj) and, for the wall value, x_ff = (i + 2 di, j + 2 dj):
+//   f'_b = f'_f + f^eq(rho_f, u_w; eps_b) - f^eq(rho_f, u_f; eps_f)
+//        = f'_f + w_q [Q(u_w, eps_b) - Q(u_f, eps_f)],  Q = 3 e.u + 4.5 (e.u)^2 / eps - 1.5 u^2 / eps
+//   g'_b = g'_f + a0/a1 (T'_b - T'_f) + (e_q . (u_w T_b - u_f T_f)) / 2           (Eq. 34)
+//   h'_b = h'_f + a_b C'_b - a_f C'_f + (e_q . (u_w C_b - u_f C_f)) / 2           (Eq. 35)
+// (the storage shifts of f, g, h cancel against those of x_f).  u_f from Eq. 18 with
+// x_f's porous constants; u_w the velocity of the wall (the bottom / top wall's at a corner).
+template <typename S, typename R>
+__device__ __forceinline__ void nee_rebuild(const S* __restrict__ buf, const Geom& G, int i, int j,
+                                            int di, int dj, const Coef<R>& c, R f[9], R g[5],
+                                            R h[5]) {
+    const int fi = i + di, fj = j + dj;
+    gather_pull<false, true, false>(buf, G, fi, fj, c, f, g, h);   // x_f is interior
+    R g2[5], h2[5], dummy[9];
+    gather_pull<false, false, false>(buf, G, i + 2 * di, j + 2 * dj, c, dummy, g2, h2);
+    Coef<R> cf = c, cb = c;
+    R inv_eps_ff = c.inv_eps;
+    if (c.poro) {
+        porous_at(cf, (size_t)fj * G.pitch + fi, G.plane);
+        porous_at(cb, (size_t)j * G.pitch + i, G.plane);
+        inv_eps_ff = R(1) / c.poro[(size_t)(j + 2 * dj) * G.pitch + (i + 2 * di)];
+    }
+    const Macro<R> M = macro(cf, f, g, h);
+    const R Tff = (((g2[0] + g2[1]) + (g2[2] + g2[3])) + g2[4]) * c.inv_sigma;   // Eq. 26
+    const R Cff = (((h2[0] + h2[1]) + (h2[2] + h2[3])) + h2[4]) * inv_eps_ff;
+    const R Tb = nee_scalar(c, di, dj, c.TwP, c.bT, M.Tp, Tff);
+    const R Cb = nee_scalar(c, di, dj, c.CwP, c.bC, M.Cp, Cff);
+    const int sv = dj ? (dj > 0 ? 2 : 3) : (di > 0 ? 0 : 1);
+    const R ubx = c.uwall[sv][0], uby = c.uwall[sv][1];
+    const R ub2 = ubx * ubx + uby * uby, uf2 = M.ux * M.ux + M.uy * M.uy;
+    const R ieb = cb.inv_eps_f, ief = cf.inv_eps_f;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const R eb = R(ex_of(q)) * ubx + R(ey_of(q)) * uby;
+        const R ef = R(ex_of(q)) * M.ux + R(ey_of(q)) * M.uy;
+        const R Qb = R(3) * eb + (R(4.5) * eb * eb - R(1.5) * ub2) * ieb;
+        const R Qf = R(3) * ef + (R(4.5) * ef * ef - R(1.5) * uf2) * ief;
+        f[q] += R(w9_of(q)) * (Qb - Qf);
+    }
+    const R TB = c.T0 + Tb, TF = c.T0 + M.Tp, CB = c.C0 + Cb, CF = c.C0 + M.Cp;
+    g[0] += c.aT0 * (Tb - M.Tp);
+    h[0] += cb.aC0 * Cb - cf.aC0 * M.Cp;
+#pragma unroll
+    for (int q = 1; q < 5; ++q) {
+        const R eb = R(ex_of(q)) * ubx + R(ey_of(q)) * uby;
+        const R ef = R(ex_of(q)) * M.ux + R(ey_of(q)) * M.uy;
+        g[q] += c.aT1 * (Tb - M.Tp) + R(0.5) * (eb * TB - ef * TF);
+        h[q] += cb.aC1 * Cb - cf.aC1 * M.Cp + R(0.5) * (eb * CB - ef * CF);
+    }
+}
+
+// Pre-collision populations of node (i, j) on a grid with wall nodes: the plain pull
+// inside (every neighbour is a node), the rebuild of Eqs. 33-35 on the walls.
+template <typename S, typename R>
+__device__ __forceinline__ void gather_nee(const S* __restrict__ buf, const Geom& G, int i, int j,
+                                           const Coef<R>& c, R f[9], R g[5], R h[5]) {
+    const int di = i == 0 ? 1 : (i == G.nx - 1 ? -1 : 0);
+    const int dj = j == 0 ? 1 : (j == G.ny - 1 ? -1 : 0);
+    if (di | dj)
+        nee_rebuild(buf, G, i, j, di, dj, c, f, g, h);
+    else
+        gather_pull<false, true, false>(buf, G, i, j, c, f, g, h);
+}
+
 // The same with the mode fixed at compile time (no code for the other two modes).
 template <int MODE, typename S, typename R>
 __device__ __forceinline__ void gather_m(const S* __restrict__ buf, const Geom& G, int i, int j,
@@ -104,6 +188,8 @@ __device__ __forceinline__ void gather_m(const S* __restrict__ buf, const Geom& 
         gather_pull<false, true>(buf, G, i, j, c, f, g, h);
     else if (MODE == GATHER_PULL_AA)
         gather_pull<true, true>(buf, G, i, j, c, f, g, h);
+    else if (MODE == GATHER_NEE_AB)
+        gather_nee(buf, G, i, j, c, f, g, h);
     else
         gather_local<true>(buf, G, i, j, f, g, h);
 }
@@ -115,6 +201,8 @@ __device__ __forceinline__ void gather(int mode, const S* __restrict__ buf, cons
         gather_pull<false, WITH_F>(buf, G, i, j, c, f, g, h);
     else if (mode == GATHER_PULL_AA)
         gather_pull<true, WITH_F>(buf, G, i, j, c, f, g, h);
+    else if (mode == GATHER_NEE_AB)
+        gather_nee(buf, G, i, j, c, f, g, h);
     else
         gather_local<WITH_F>(buf, G, i, j, f, g, h);
 }
@@ -229,6 +317,50 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
     uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
     collide_node<EXT>(c, self, G.plane, f, g, h, hv);
     store_ab(dst, G, self, c, f, g, h, seed);
+    store_hist(hist, G, self, hv);
+}
+
+// ---- the fused step with wall nodes (Sec. 3.3), two-buffer pull layout ---------------
+// Inside: the plain pull.  Wall nodes: the populations rebuilt by Eqs. 33-35 (from
+// the post-streaming populations of x_f and x_ff, both pulled from src), then the
+// same collision as every node.
+template <typename S>
+__global__ void __launch_bounds__(256)
+step_nee_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                typename Real<S>::type* __restrict__ hist, Geom G,
+                Coef<typename Real<S>::type> c) {
+    using R = typename Real<S>::type;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    R f[9], g[5], h[5], hv[4];
+    const size_t self = (size_t)j * G.pitch + i;
+    gather_nee(src, G, i, j, c, f, g, h);
+    load_hist(hist, G, self, hv);
+    uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
+    collide_node<true>(c, self, G.plane, f, g, h, hv);
+    store_ab(dst, G, self, c, f, g, h, seed);
+    store_hist(hist, G, self, hv);
+}
+
+// History (T u, C u) at t = 0 of the wall nodes, from their rebuilt initial state
+// (init_kernel wrote the interior's and the buffer the pull reads).
+template <typename S>
+__global__ void nee_hist_kernel(const S* __restrict__ buf, typename Real<S>::type* __restrict__ hist,
+                                Geom G, Coef<typename Real<S>::type> c) {
+    using R = typename Real<S>::type;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= G.nx || j >= G.ny) return;
+    if (i > 0 && i < G.nx - 1 && j > 0 && j < G.ny - 1) return;
+    R f[9], g[5], h[5];
+    gather_nee(buf, G, i, j, c, f, g, h);
+    const size_t self = (size_t)j * G.pitch + i;
+    Coef<R> cl = c;
+    if (c.poro) porous_at(cl, self, G.plane);
+    const Macro<R> M = macro(cl, f, g, h);
+    const R T = c.T0 + M.Tp, C = c.C0 + M.Cp;
+    const R hv[4] = {T * M.ux, T * M.uy, C * M.ux, C * M.uy};
     store_hist(hist, G, self, hv);
 }
 
@@ -423,7 +555,30 @@ nush_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c, i
             WallSpec W, double* __restrict__ out) {
     using R = typename Real<S>::type;
     double acc[4] = {0, 0, 0, 0};
-    for (int j = threadIdx.x; j < G.ny; j += blockDim.x) {
+    if (W.nee) {
+        // nodes on the walls: dPhi/dx|wall = (-3 Phi_0 + 4 Phi_1 - Phi_2) / 2, mirrored on
+        // the right; trapezoidal mean over the ny - 1 spacings
+        for (int j = threadIdx.x; j < G.ny; j += blockDim.x) {
+            R f[9], g[5], h[5];
+            double T[6], C[6];
+            const int cols[6] = {0, 1, 2, G.nx - 3, G.nx - 2, G.nx - 1};
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                gather<false>(mode, buf, G, cols[k], j, c, f, g, h);
+                const R sg = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+                const R sh = ((h[0] + h[1]) + (h[2] + h[3])) + h[4];
+                const R ie = c.poro ? R(1) / c.poro[(size_t)j * G.pitch + cols[k]] : c.inv_eps;
+                T[k] = W.T0 + (double)(sg * c.inv_sigma);
+                C[k] = W.C0 + (double)(sh * ie);
+            }
+            const double wj = (j == 0 || j == G.ny - 1) ? 0.5 : 1.0;
+            acc[0] += wj * -W.L * (-3.0 * T[0] + 4.0 * T[1] - T[2]) / 2.0 / W.dT;
+            acc[1] += wj * -W.L * (-3.0 * C[0] + 4.0 * C[1] - C[2]) / 2.0 / W.dC;
+            acc[2] += wj * -W.L * (3.0 * T[5] - 4.0 * T[4] + T[3]) / 2.0 / W.dT;
+            acc[3] += wj * -W.L * (3.0 * C[5] - 4.0 * C[4] + C[3]) / 2.0 / W.dC;
+        }
+    }
+    for (int j = threadIdx.x; j < G.ny && !W.nee; j += blockDim.x) {
         R f[9], g[5], h[5];
         double T[4], C[4];
         const int cols[4] = {0, 1, G.nx - 2, G.nx - 1};
@@ -453,7 +608,7 @@ nush_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c, i
     if (threadIdx.x < 4) {
         double s = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-        out[threadIdx.x] = s / G.ny;
+        out[threadIdx.x] = s / (W.nee ? G.ny - 1.0 : (double)G.ny);
     }
 }
 
@@ -465,7 +620,29 @@ nush_tb_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c
                WallSpec W, double* __restrict__ out) {
     using R = typename Real<S>::type;
     double acc[4] = {0, 0, 0, 0};
-    for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
+    if (W.nee) {
+        // as on the left / right walls, transposed (node stencil, trapezoidal mean over x)
+        for (int i = threadIdx.x; i < G.nx; i += blockDim.x) {
+            R f[9], g[5], h[5];
+            double T[6], C[6];
+            const int rows[6] = {0, 1, 2, G.ny - 3, G.ny - 2, G.ny - 1};
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                gather<false>(mode, buf, G, i, rows[k], c, f, g, h);
+                const R sg = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+                const R sh = ((h[0] + h[1]) + (h[2] + h[3])) + h[4];
+                const R ie = c.poro ? R(1) / c.poro[(size_t)rows[k] * G.pitch + i] : c.inv_eps;
+                T[k] = W.T0 + (double)(sg * c.inv_sigma);
+                C[k] = W.C0 + (double)(sh * ie);
+            }
+            const double wi = (i == 0 || i == G.nx - 1) ? 0.5 : 1.0;
+            acc[0] += wi * W.L * (-3.0 * T[0] + 4.0 * T[1] - T[2]) / 2.0 / W.dT;
+            acc[1] += wi * W.L * (-3.0 * C[0] + 4.0 * C[1] - C[2]) / 2.0 / W.dC;
+            acc[2] += wi * W.L * (3.0 * T[5] - 4.0 * T[4] + T[3]) / 2.0 / W.dT;
+            acc[3] += wi * W.L * (3.0 * C[5] - 4.0 * C[4] + C[3]) / 2.0 / W.dC;
+        }
+    }
+    for (int i = threadIdx.x; i < G.nx && !W.nee; i += blockDim.x) {
         R f[9], g[5], h[5];
         double T[4], C[4];
         const int rows[4] = {0, 1, G.ny - 2, G.ny - 1};
@@ -495,7 +672,7 @@ nush_tb_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c
     if (threadIdx.x < 4) {
         double s = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-        out[threadIdx.x] = s / G.nx;
+        out[threadIdx.x] = s / (W.nee ? G.nx - 1.0 : (double)G.nx);
     }
 }
 
@@ -591,6 +768,7 @@ cudaError_t launch_residual_pass1(const S* buf, const Geom& G, const Coef<typena
     LBM_RES_CASE(GATHER_PULL_AB)
     LBM_RES_CASE(GATHER_PULL_AA)
     LBM_RES_CASE(GATHER_LOCAL)
+    LBM_RES_CASE(GATHER_NEE_AB)
 #undef LBM_RES_CASE
     return cudaErrorInvalidValue;
 }

@@ -18,7 +18,7 @@ struct Geom {
 };
 
 // How the pre-collision populations of the current level are read.
-enum { GATHER_LOCAL = 0, GATHER_PULL_AB = 1, GATHER_PULL_AA = 2 };
+enum { GATHER_LOCAL = 0, GATHER_PULL_AB = 1, GATHER_PULL_AA = 2, GATHER_NEE_AB = 3 };
 
 struct InitSpec {
     const double* T_init;   // device [ny][nx] or NULL (noise)
@@ -32,6 +32,7 @@ struct InitSpec {
 struct WallSpec {
     double Tw[2], Cw[2];    // absolute wall values, left / right
     double T0, C0, dT, dC, L;
+    int nee;                // 1: nodes on the walls (node stencil, trapezoidal mean)
 };
 
 constexpr int NUSH_THREADS = 512;

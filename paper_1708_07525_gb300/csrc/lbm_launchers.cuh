@@ -18,6 +18,11 @@ cudaError_t launch_init(void* buf, void* hist, const Geom& G, const Coef<typenam
         init_kernel<S, true><<<gr, b, 0, st>>>((S*)buf, (R*)hist, G, c, I);
     else
         init_kernel<S, false><<<gr, b, 0, st>>>((S*)buf, (R*)hist, G, c, I);
+    if (c.nee && pull) {   // wall nodes: the t = 0 state obeys the wall rules too
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        nee_hist_kernel<S><<<gr, b, 0, st>>>((const S*)buf, (R*)hist, G, c);
+    }
     return cudaGetLastError();
 }
 
@@ -26,7 +31,9 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
                            const Coef<typename Real<S>::type>& c, const LaunchCfg& L) {
     using R = typename Real<S>::type;
     dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
-    if (c.poro || c.moving)
+    if (c.nee)
+        step_nee_kernel<S><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+    else if (c.poro || c.moving)
         step_ab_kernel<S, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
     else
         step_ab_kernel<S, false><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);

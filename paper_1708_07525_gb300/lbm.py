@@ -60,7 +60,7 @@ class lbm_params(C.Structure):
         ("C0", C.c_double), ("s", C.c_double * 9), ("zeta", C.c_double * 5),
         ("eta", C.c_double * 5), ("Tw", C.c_double * 4), ("Cw", C.c_double * 4),
         ("wall_lr", C.c_int), ("wall_tb", C.c_int), ("uw", (C.c_double * 2) * 4),
-        ("model_a", C.c_int),
+        ("model_a", C.c_int), ("nee", C.c_int), ("BiT", C.c_double * 4), ("BiC", C.c_double * 4),
     ]
 
 
@@ -86,6 +86,9 @@ def lib():
                                          C.POINTER(C.c_void_p)]
             L.lbm_params_model_a.argtypes = [C.POINTER(lbm_params)]
             L.lbm_derive_params_lid.argtypes = [lbm_grid] + [C.c_double] * 11 + [C.POINTER(lbm_params)]
+            L.lbm_derive_params_nee.argtypes = [lbm_grid] + [C.c_double] * 10 + [C.POINTER(lbm_params)]
+            L.lbm_derive_params_convective.argtypes = ([C.c_int] + [C.c_double] * 12
+                                                       + [C.POINTER(lbm_params)])
             L.lbm_nusselt_sherwood_tb.argtypes = [P, dp]
             L.lbm_reset.argtypes = [P, dp, dp, C.c_uint64, C.c_double]
             L.lbm_step.argtypes = [P, C.c_int64]
@@ -105,6 +108,7 @@ def lib():
             L.lbm_last_error.argtypes = [P]
             L.lbm_last_error.restype = C.c_char_p
             for name in ("lbm_derive_params", "lbm_params_model_a", "lbm_derive_params_lid",
+                         "lbm_derive_params_nee", "lbm_derive_params_convective",
                          "lbm_nusselt_sherwood_tb", "lbm_create", "lbm_create_raw",
                          "lbm_reset", "lbm_step",
                          "lbm_fields", "lbm_fields_window", "lbm_nusselt_sherwood", "lbm_residual",
@@ -168,6 +172,24 @@ def lbm_derive_params_lid(nx, ny, Re, Gr, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, 
     p = lbm_params()
     _check(lib().lbm_derive_params_lid(lbm_grid(int(nx), int(ny)), Re, Gr, Da, eps, Pr, Le, N, J,
                                        sigma, U0, varpi, C.byref(p)))
+    return p
+
+
+def lbm_derive_params_nee(nx, ny, Ra, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, Ma=0.0, varpi=0.0):
+    """lbm_derive_params for walls with nodes on them (Sec. 3.3), L = nx - 1."""
+    p = lbm_params()
+    _check(lib().lbm_derive_params_nee(lbm_grid(int(nx), int(ny)), Ra, Da, eps, Pr, Le, N, J, sigma,
+                                       Ma, varpi, C.byref(p)))
+    return p
+
+
+def lbm_derive_params_convective(Nx, Ra, Da, eps, Pr, Le, N, BiT, BiC, J=1.0, sigma=1.0, Ma=0.0,
+                                 varpi=0.0):
+    """The porous cavity with a freely convective right wall of Sec. 4.2 (Nx spacings,
+    Nx + 1 nodes per side on the walls)."""
+    p = lbm_params()
+    _check(lib().lbm_derive_params_convective(int(Nx), Ra, Da, eps, Pr, Le, N, BiT, BiC, J, sigma,
+                                              Ma, varpi, C.byref(p)))
     return p
 
 

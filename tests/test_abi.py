@@ -71,3 +71,37 @@ def test_rate_outside_stable_range_rejected():
         lbm.Cavity(params=p, allocator=None)
     assert ei.value.status == lbm.ERR_INVALID
     assert "relaxation rate" in str(ei.value)
+
+
+def test_derive_nee_and_convective_match_the_oracle(oracle_mod):
+    """The node-on-wall mapping (L = nx - 1) and the Sec. 4.2 convective cavity agree
+    with the oracle's independent derivation, field by field."""
+    O = oracle_mod
+    pairs = [(lbm.lbm_derive_params_nee(21, 13, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0, sigma=0.8),
+              O.derive(21, 13, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0, sigma=0.8, nee=True)),
+             (lbm.lbm_derive_params_convective(40, 1e4, 1e-2, 0.6, 1.0, 1.0, 1.0, 1.0, 200.0),
+              O.derive_convective(40, 1e4, 1e-2, 0.6, 1.0, 1.0, 1.0, 1.0, 200.0))]
+    for g, o in pairs:
+        assert (g.nx, g.ny, g.nee) == (o.nx, o.ny, 1)
+        for k in ("eps", "sigma", "varpi", "nu", "K", "Feps", "gbT", "gbC", "T0", "C0"):
+            assert abs(getattr(g, k) - getattr(o, k)) <= 1e-15 * max(1.0, abs(getattr(o, k))), k
+        for k in ("s", "zeta", "eta", "Tw", "Cw", "BiT", "BiC"):
+            np.testing.assert_allclose(list(getattr(g, k)), list(getattr(o, k)), rtol=1e-15, atol=0)
+    g = pairs[1][0]
+    assert (g.nx, g.ny) == (41, 41) and g.BiT[1] == 1.0 and g.BiC[1] == 200.0
+    # L = 40 spacings: K = Da L^2
+    assert abs(g.K - 1e-2 * 40 * 40) < 1e-12
+
+
+def test_nee_misuse_rejected():
+    p = lbm.lbm_derive_params(16, 16, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
+    p.BiT[1] = 1.0                        # a convective wall needs wall nodes
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Cavity(params=p, allocator=None)
+    assert "nee" in str(ei.value)
+    q = lbm.lbm_derive_params_nee(16, 16, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
+    with pytest.raises(lbm.LbmError) as ei:   # the rebuild reads the two-buffer pull layout
+        lbm.Cavity(params=q, layout="aa", allocator=None)
+    assert ei.value.status == lbm.ERR_INVALID
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_derive_params_nee(4, 16, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
