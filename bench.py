@@ -226,9 +226,17 @@ def run_ours(args):
     spec = throughput_cavity(n)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    cav = lbm.Cavity(*spec.args(), precision=args.precision, layout=args.layout,
-                     seed=spec.seed + rank, noise=spec.noise, stream=stream.cuda_stream,
-                     block=(args.bx, args.by))
+    if args.walls == "nee":
+        # the paper's own walls (Sec. 3.3): nodes on the walls, L = n - 1
+        p = lbm.lbm_derive_params_nee(n, n, spec.Ra, spec.Da, spec.eps, spec.Pr, spec.Le, spec.N,
+                                      spec.J, spec.sigma, 0.0, spec.varpi)
+        cav = lbm.Cavity(params=p, precision=args.precision, layout=args.layout,
+                         seed=spec.seed + rank, noise=spec.noise, stream=stream.cuda_stream,
+                         block=(args.bx, args.by))
+    else:
+        cav = lbm.Cavity(*spec.args(), precision=args.precision, layout=args.layout,
+                         seed=spec.seed + rank, noise=spec.noise, stream=stream.cuda_stream,
+                         block=(args.bx, args.by))
     k = STEPS_PER_BENCH_STEP
 
     def bench_step(ev_pair=None):
@@ -294,7 +302,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     bpn = BYTES_PER_NODE[args.precision]
     achieved = nodes * bpn / (kernel_ms / 1e3) / 1e9
-    kname = f"step_{args.layout}_{args.precision}_{n}"
+    kname = f"step_{args.layout}_{args.precision}_{n}" + ("_nee" if args.walls == "nee" else "")
     traffic = profiled_traffic(kname)
     line = {
         "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
@@ -303,7 +311,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {
             "workload": f"porous cavity {n}x{n}, Ra=1e5 Da=1e-3 eps=0.4 Pr=1 Le=5 N=-1, "
-                        f"{args.precision} {'two-buffer pull' if args.layout == 'ab' else 'in-place AA'}",
+                        f"{args.precision} {'two-buffer pull' if args.layout == 'ab' else 'in-place AA'}"
+                        + (", wall nodes (Sec. 3.3)" if args.walls == "nee" else ", halfway walls"),
             "nx": n, "ny": n, "time_steps_per_bench_step": k,
             "bench_step": f"{k} fused time steps + FP64 Nu/Sh reduction + residual",
             "l2": "state larger than L2 (no flush needed)" if nodes * bpn / 2 > 129e6
@@ -313,7 +322,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",
-                     "kernel": f"step_{args.layout}_kernel<{args.precision}>",
+                     "kernel": (f"step_nee_kernel<{args.precision}>" if args.walls == "nee"
+                                else f"step_{args.layout}_kernel<{args.precision}>"),
                      "kernel_us_per_launch": kernel_ms * 1e3,
                      "algorithmic_bytes_per_node": bpn,
                      "frac_19_distribution_convention":
@@ -567,6 +577,8 @@ def main():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16", "f16"])
     ap.add_argument("--layout", default="ab", choices=["ab", "aa"])
+    ap.add_argument("--walls", default="halfway", choices=["halfway", "nee"],
+                    help="step mode: halfway walls (the workload's) or wall nodes (Sec. 3.3)")
     ap.add_argument("--bx", type=int, default=0)
     ap.add_argument("--by", type=int, default=0)
     ap.add_argument("--ref-steps", type=int, default=1)

@@ -49,6 +49,21 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     return x;
 }
 
+template <typename R> __device__ __forceinline__ R sqrt_(R x);
+template <> __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+// |x|, max(a, b) and finiteness in the precision of the argument (FP32 stays on the
+// FP32 pipes; GB300's FP64 pipe is narrow).
+template <typename R> __device__ __forceinline__ R abs_(R x);
+template <> __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+template <> __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+template <typename R> __device__ __forceinline__ R max_(R a, R b);
+template <> __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
+template <> __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
+template <typename R> __device__ __forceinline__ bool finite_(R x);
+template <> __device__ __forceinline__ bool finite_(float x) { return fabsf(x) <= 3.402823466e38f; }
+template <> __device__ __forceinline__ bool finite_(double x) { return fabs(x) <= 1.7976931348623157e308; }
+
 // st() rounds to nearest even; st_sr() rounds stochastically (up with probability
 // equal to the distance to the lower neighbour in ulps), so that the expected stored
 // value equals the computed one.  With 8-11 significand bits, rounding to nearest
@@ -72,11 +87,10 @@ template <> struct Store<__nv_bfloat16> {
     __device__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     __device__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
     __device__ static void st_sr(__nv_bfloat16* p, float v, uint32_t r) {
-        // bfloat16 is the top half of the float: add 16 random bits below it, truncate
-        // (on the sign-magnitude encoding this rounds |v| away from zero with the right
-        // odds).  Non-finite values pass unchanged (their low bits are not touched).
-        uint32_t b = __float_as_uint(v);
-        b += ((b & 0x7F800000u) != 0x7F800000u) ? (r & 0xFFFFu) : 0u;
+        // bfloat16 is the top half of the float: add 16 random bits (r < 2^16) below it,
+        // truncate (on the sign-magnitude encoding this rounds |v| away from zero with
+        // the right odds).  v must be finite (put() routes non-finite nodes to st()).
+        const uint32_t b = __float_as_uint(v) + r;
         *p = __ushort_as_bfloat16((unsigned short)(b >> 16));
     }
 };
@@ -90,25 +104,39 @@ template <> struct Store<__half> {
     __device__ static void st(__half* p, float v) { *p = __float2half_rn(v * kScale); }
     __device__ static void st_sr(__half* p, float v, uint32_t r) {
         // In FP16's normal range the 13 float mantissa bits below the 10 kept ones are
-        // the fraction of an FP16 ulp: add 13 random bits there, then truncate.
-        uint32_t b = __float_as_uint(v * kScale);
-        b += ((b & 0x7F800000u) != 0x7F800000u) ? (r & 0x1FFFu) : 0u;
+        // the fraction of an FP16 ulp: add 13 random bits there, then truncate.  v must
+        // be finite (put() routes non-finite nodes to st()).
+        const uint32_t b = __float_as_uint(v * kScale) + (r & 0x1FFFu);
         *p = __float2half_rz(__uint_as_float(b));
     }
 };
 
 // Store one of a node's populations: stochastic rounding for 16-bit storage when
-// enabled.  The random bits come from a per-node linear congruential stream
-// (Knuth's MMIX constants) seeded by node_seed(); only its high 16 bits are used,
-// which is enough for rounding decisions and costs one multiply-add per value.
+// sr is set (see sr_node).  The random bits come from a per-node linear
+// congruential stream (Knuth's MMIX constants) seeded by node_seed(); only its high
+// 16 bits are used, which is enough for rounding decisions and costs one
+// multiply-add per value.
 template <typename S, typename R>
 __device__ __forceinline__ void put(S* p, R v, int sr, uint32_t& state, int) {
     if (Store<S>::kLow && sr) {
         state = state * 1664525u + 1013904223u;
-        Store<S>::st_sr(p, v, (state >> 16) | (state & 0xFFFF0000u));
+        Store<S>::st_sr(p, v, state >> 16);
     } else {
         Store<S>::st(p, v);
     }
+}
+
+// Whether a node's post-collision values are stored with stochastic rounding: 16-bit
+// storage with rounding enabled and all 19 values finite (one check on their sum
+// instead of one per value; a node holding a NaN or an infinity is rounded to
+// nearest, which keeps it non-finite for the residual's divergence check).
+template <typename S, typename R>
+__device__ __forceinline__ int sr_node(int sr, const R f[9], const R g[5], const R h[5]) {
+    if (!Store<S>::kLow || !sr) return 0;
+    R s = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]));
+    s += ((f[8] + g[0]) + (g[1] + g[2])) + ((g[3] + g[4]) + (h[0] + h[1]));
+    s += (h[2] + h[3]) + h[4];
+    return finite_(s) ? 1 : 0;
 }
 
 // Per-node seed of the random stream: a hash of the node's index and of the bits of
@@ -163,20 +191,6 @@ struct Coef {
 };
 
 
-template <typename R> __device__ __forceinline__ R sqrt_(R x);
-template <> __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-// |x|, max(a, b) and finiteness in the precision of the argument (FP32 stays on the
-// FP32 pipes; GB300's FP64 pipe is narrow).
-template <typename R> __device__ __forceinline__ R abs_(R x);
-template <> __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
-template <> __device__ __forceinline__ double abs_(double x) { return fabs(x); }
-template <typename R> __device__ __forceinline__ R max_(R a, R b);
-template <> __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
-template <> __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
-template <typename R> __device__ __forceinline__ bool finite_(R x);
-template <> __device__ __forceinline__ bool finite_(float x) { return fabsf(x) <= 3.402823466e38f; }
-template <> __device__ __forceinline__ bool finite_(double x) { return fabs(x) <= 1.7976931348623157e308; }
 
 // The constants of node `self` of a cavity with a porosity / permeability field:
 // eps and K from the field, F_eps from Eq. 7, l0 and l1 from Eq. 19, the drag

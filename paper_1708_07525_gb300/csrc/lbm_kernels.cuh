@@ -44,10 +44,42 @@ __device__ __forceinline__ R wall_momentum(const Coef<R>& c, int side, int q) {
 // SWAP = true: in-place AA layout after an even step, slot opp(q) of the source.
 // EXT: the cavity may have moving walls (checked at run time); without it the
 // moving-wall code is not compiled in (the fast path of the plain cavity).
+// Nodes whose eight neighbours all lie in the cavity (every node but the outermost
+// ring) can take a path with no wall rule, where each address is the node's own plus
+// an offset that is the same for every thread (kept in uniform registers).  Taken
+// for 16-bit storage in the two-buffer layout, whose kernels are issue-bound: it
+// saves ~10 % there (GB300, 4096^2); the FP32 kernels are DRAM-bound and measured
+// 3 % (two-buffer) and 13 % (in-place) slower with it, so they keep one path.
+template <bool SWAP, bool WITH_F, typename S, typename R>
+__device__ __forceinline__ void gather_pull_inner(const S* __restrict__ buf, const Geom& G,
+                                                  size_t self, R f[9], R g[5], R h[5]) {
+    const S* p = buf + self;
+    if (WITH_F) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const long long off = (long long)(QF + (SWAP ? opp_of(q) : q)) * (long long)G.plane -
+                                  ex_of(q) - (long long)ey_of(q) * G.pitch;
+            f[q] = Store<S>::ld(p + off);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const long long d = -(long long)ex_of(q) - (long long)ey_of(q) * G.pitch;
+        const int slot = SWAP ? opp_of(q) : q;
+        g[q] = Store<S>::ld(p + ((long long)(QG + slot) * (long long)G.plane + d));
+        h[q] = Store<S>::ld(p + ((long long)(QH + slot) * (long long)G.plane + d));
+    }
+}
+
 template <bool SWAP, bool WITH_F, bool EXT = true, typename S, typename R>
 __device__ __forceinline__ void gather_pull(const S* __restrict__ buf, const Geom& G, int i, int j,
                                             const Coef<R>& c, R f[9], R g[5], R h[5]) {
     const size_t self = (size_t)j * G.pitch + i;
+    if (Store<S>::kLow && !SWAP && (unsigned)(i - 1) < (unsigned)(G.nx - 2) &&
+        (unsigned)(j - 1) < (unsigned)(G.ny - 2)) {
+        gather_pull_inner<SWAP, WITH_F>(buf, G, self, f, g, h);
+        return;
+    }
     if (WITH_F) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
@@ -226,12 +258,13 @@ template <typename S, typename R>
 __device__ __forceinline__ void store_ab(S* __restrict__ dst, const Geom& G, size_t self,
                                          const Coef<R>& c, const R f[9], const R g[5],
                                          const R h[5], uint32_t& seed) {
+    const int sr = sr_node<S>(c.sr, f, g, h);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) put(dst + (size_t)(QF + q) * G.plane + self, f[q], c.sr, seed, q);
+    for (int q = 0; q < 9; ++q) put(dst + (size_t)(QF + q) * G.plane + self, f[q], sr, seed, q);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        put(dst + (size_t)(QG + q) * G.plane + self, g[q], c.sr, seed, QG + q);
-        put(dst + (size_t)(QH + q) * G.plane + self, h[q], c.sr, seed, QH + q);
+        put(dst + (size_t)(QG + q) * G.plane + self, g[q], sr, seed, QG + q);
+        put(dst + (size_t)(QH + q) * G.plane + self, h[q], sr, seed, QH + q);
     }
 }
 
@@ -240,13 +273,14 @@ template <typename S, typename R>
 __device__ __forceinline__ void store_aa_even(S* __restrict__ buf, const Geom& G, size_t self,
                                               const Coef<R>& c, const R f[9], const R g[5],
                                               const R h[5], uint32_t& seed) {
+    const int sr = sr_node<S>(c.sr, f, g, h);
 #pragma unroll
     for (int q = 0; q < 9; ++q)
-        put(buf + (size_t)(QF + opp_of(q)) * G.plane + self, f[q], c.sr, seed, q);
+        put(buf + (size_t)(QF + opp_of(q)) * G.plane + self, f[q], sr, seed, q);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        put(buf + (size_t)(QG + opp_of(q)) * G.plane + self, g[q], c.sr, seed, QG + q);
-        put(buf + (size_t)(QH + opp_of(q)) * G.plane + self, h[q], c.sr, seed, QH + q);
+        put(buf + (size_t)(QG + opp_of(q)) * G.plane + self, g[q], sr, seed, QG + q);
+        put(buf + (size_t)(QH + opp_of(q)) * G.plane + self, h[q], sr, seed, QH + q);
     }
 }
 
@@ -256,6 +290,7 @@ template <bool EXT = true, typename S, typename R>
 __device__ __forceinline__ void store_aa_odd(S* __restrict__ buf, const Geom& G, int i, int j,
                                              size_t self, const Coef<R>& c, const R f[9],
                                              const R g[5], const R h[5], uint32_t& seed) {
+    const int sr = sr_node<S>(c.sr, f, g, h);   // the wall rules add finite constants
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const int ti = i + ex_of(q), tj = j + ey_of(q);
@@ -264,7 +299,7 @@ __device__ __forceinline__ void store_aa_odd(S* __restrict__ buf, const Geom& G,
                   : buf + (size_t)(QF + opp_of(q)) * G.plane + self;
         R v = f[q];
         if (EXT && !in && c.moving) v -= wall_momentum(c, link_side(ti, tj, G), q);
-        put(p, v, c.sr, seed, q);
+        put(p, v, sr, seed, q);
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -280,8 +315,8 @@ __device__ __forceinline__ void store_aa_odd(S* __restrict__ buf, const Geom& G,
             vg = wall_value(c, c.wallT, push_side(q), vg);
             vh = wall_value(c, c.wallC, push_side(q), vh);
         }
-        put(buf + (size_t)(QG + slot) * G.plane + off, vg, c.sr, seed, QG + q);
-        put(buf + (size_t)(QH + slot) * G.plane + off, vh, c.sr, seed, QH + q);
+        put(buf + (size_t)(QG + slot) * G.plane + off, vg, sr, seed, QG + q);
+        put(buf + (size_t)(QH + slot) * G.plane + off, vh, sr, seed, QH + q);
     }
 }
 
