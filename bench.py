@@ -322,7 +322,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",
-                     "kernel": (f"step_nee_kernel<{args.precision}>" if args.walls == "nee"
+                     "kernel": (f"step_ab_kernel<{args.precision}> (inner nodes) + nee_ring_kernel"
+                                if args.walls == "nee"
                                 else f"step_{args.layout}_kernel<{args.precision}>"),
                      "kernel_us_per_launch": kernel_ms * 1e3,
                      "algorithmic_bytes_per_node": bpn,

@@ -336,7 +336,9 @@ __device__ __forceinline__ void collide_node(const Coef<R>& c, size_t self, size
 
 // ---- the fused step, two-buffer pull layout ---------------------------------------
 // EXT = true for cavities with moving walls or porous fields, false otherwise.
-template <typename S, bool EXT>
+// INNER = true: the outermost ring of nodes is left to nee_ring_kernel (walls with
+// nodes on them), so this kernel keeps the plain pull's registers and occupancy.
+template <typename S, bool EXT, bool INNER = false>
 __global__ void __launch_bounds__(256)
 step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
                typename Real<S>::type* __restrict__ hist, Geom G,
@@ -345,6 +347,8 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= G.nx || j >= G.ny) return;
+    if (INNER && !((unsigned)(i - 1) < (unsigned)(G.nx - 2) && (unsigned)(j - 1) < (unsigned)(G.ny - 2)))
+        return;
     R f[9], g[5], h[5], hv[4];
     const size_t self = (size_t)j * G.pitch + i;
     gather_pull<false, true, EXT>(src, G, i, j, c, f, g, h);
@@ -356,18 +360,30 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
 }
 
 // ---- the fused step with wall nodes (Sec. 3.3), two-buffer pull layout ---------------
-// Inside: the plain pull.  Wall nodes: the populations rebuilt by Eqs. 33-35 (from
-// the post-streaming populations of x_f and x_ff, both pulled from src), then the
-// same collision as every node.
+// The inner nodes take step_ab_kernel<S, EXT, true> (the plain pull); this kernel
+// takes the ring of wall nodes, k = 0 .. 2 nx + 2 (ny - 2) - 1 (bottom row, top row,
+// left column, right column): populations rebuilt by Eqs. 33-35 from the
+// post-streaming populations of x_f and x_ff (both pulled from src, which no
+// launch of this step writes), then the same collision as every node.
 template <typename S>
 __global__ void __launch_bounds__(256)
-step_nee_kernel(const S* __restrict__ src, S* __restrict__ dst,
+nee_ring_kernel(const S* __restrict__ src, S* __restrict__ dst,
                 typename Real<S>::type* __restrict__ hist, Geom G,
                 Coef<typename Real<S>::type> c) {
     using R = typename Real<S>::type;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nring = 2LL * G.nx + 2LL * (G.ny - 2);
+    if (k >= nring) return;
+    int i, j;
+    if (k < G.nx) {
+        i = (int)k; j = 0;
+    } else if (k < 2LL * G.nx) {
+        i = (int)(k - G.nx); j = G.ny - 1;
+    } else if (k < 2LL * G.nx + (G.ny - 2)) {
+        i = 0; j = (int)(k - 2LL * G.nx) + 1;
+    } else {
+        i = G.nx - 1; j = (int)(k - 2LL * G.nx - (G.ny - 2)) + 1;
+    }
     R f[9], g[5], h[5], hv[4];
     const size_t self = (size_t)j * G.pitch + i;
     gather_nee(src, G, i, j, c, f, g, h);

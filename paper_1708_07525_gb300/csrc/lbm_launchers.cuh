@@ -31,9 +31,18 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
                            const Coef<typename Real<S>::type>& c, const LaunchCfg& L) {
     using R = typename Real<S>::type;
     dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
-    if (c.nee)
-        step_nee_kernel<S><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
-    else if (c.poro || c.moving)
+    if (c.nee) {
+        // inner nodes: the plain pull; the ring of wall nodes: the rebuild (Sec. 3.3)
+        if (c.poro)
+            step_ab_kernel<S, true, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+        else
+            step_ab_kernel<S, false, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const long long nring = 2LL * G.nx + 2LL * (G.ny - 2);
+        nee_ring_kernel<S><<<(unsigned)((nring + 127) / 128), 128, 0, L.stream>>>(
+            (const S*)src, (S*)dst, (R*)hist, G, c);
+    } else if (c.poro || c.moving)
         step_ab_kernel<S, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
     else
         step_ab_kernel<S, false><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
