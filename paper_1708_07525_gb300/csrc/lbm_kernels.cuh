@@ -119,12 +119,12 @@ __device__ __forceinline__ void gather_local(const S* __restrict__ buf, const Ge
     const size_t self = (size_t)j * G.pitch + i;
     if (WITH_F) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) f[q] = Store<S>::ld(buf + (size_t)(QF + q) * G.plane + self);
+        for (int q = 0; q < 9; ++q) f[q] = Store<S>::ld_nc(buf + (size_t)(QF + q) * G.plane + self);
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        g[q] = Store<S>::ld(buf + (size_t)(QG + q) * G.plane + self);
-        h[q] = Store<S>::ld(buf + (size_t)(QH + q) * G.plane + self);
+        g[q] = Store<S>::ld_nc(buf + (size_t)(QG + q) * G.plane + self);
+        h[q] = Store<S>::ld_nc(buf + (size_t)(QH + q) * G.plane + self);
     }
 }
 
