@@ -206,3 +206,20 @@ def test_tables_2_3_gpu_against_stored_oracle(case):
     alpha = pg.nu / 1.0
     assert abs(stream_max(fl["ux"]) / alpha - rec["psi_max_over_alpha"]) < 1e-7
     gpu.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "f16"])
+def test_convective_cavity_16bit_storage(oracle_mod, precision):
+    """16-bit storage with the rebuild: the wall values are imposed in the FP32 arithmetic
+    of the read-out (the rebuilt g sums to sigma T_w whatever x_f stored), and the fields
+    follow the FP64 oracle within the rounding noise of 8-11 significant bits."""
+    gpu, ora = convective_pair(oracle_mod, 40, 200.0, precision=precision)
+    gpu.step(1000)
+    ora.step(1000)
+    fg, fo = gpu.fields(), ora.fields()
+    np.testing.assert_allclose(fg["T"][:, 0], 1.0, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(fg["C"][:, 0], 1.0, rtol=0, atol=1e-6)
+    for k in ("T", "C"):
+        assert rel_l2(fg[k], fo[k]) <= 2e-2, (k, rel_l2(fg[k], fo[k]))
+    assert np.isfinite(gpu.nusselt_sherwood()).all()
+    gpu.close()
