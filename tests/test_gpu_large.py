@@ -109,3 +109,53 @@ def test_window_and_empty_step_edges():
         with pytest.raises(lbm.LbmError) as ei:
             cav.fields_window(*bad)
         assert ei.value.status == lbm.ERR_INVALID
+
+
+def test_wall_nodes_4096_f32_sampled(oracle_mod):
+    """The paper's own walls (Sec. 3.3) on the 4096^2 benchmark cavity in the benchmark's
+    launch configuration (inner kernel + wall-ring kernel), checked on windows at the
+    four corners and two walls.  The rebuild reads two nodes in from the wall, so the
+    trusted region keeps steps + 2 nodes away from a window's artificial edges."""
+    O = oracle_mod
+    spec = throughput_cavity(4096)
+    n, steps = spec.nx, 30
+    p = lbm.lbm_derive_params_nee(n, n, spec.Ra, spec.Da, spec.eps, spec.Pr, spec.Le, spec.N)
+    cav = lbm.Cavity(params=p, precision="f32", seed=spec.seed, noise=spec.noise)
+    cav.step(steps)
+    wins = [(0, 0, 80, 80), (n - 80, 0, 80, 80), (0, n - 80, 80, 80), (n - 80, n - 80, 80, 80),
+            (0, 2000, 80, 80), (2000, n - 80, 80, 80)]
+    nfull = n * n
+    for (x0, y0, w, h) in wins:
+        po = O.derive(n, n, spec.Ra, spec.Da, spec.eps, spec.Pr, spec.Le, spec.N, nee=True)
+        po.nx, po.ny = w, h                 # constants of the full grid, window extent
+        jj, ii = np.mgrid[0:h, 0:w]
+        k = (y0 + jj) * n + (x0 + ii)
+        T = 0.5 + spec.noise * (2.0 * np.vectorize(lambda q: O.uniform(spec.seed, int(q)))(k) - 1.0)
+        C = 0.5 + spec.noise * (2.0 * np.vectorize(lambda q: O.uniform(spec.seed, int(nfull + q)))(k) - 1.0)
+        o = O.Oracle(po, seed=spec.seed, noise=spec.noise, T_init=T, C_init=C)
+        o.step(steps)
+        fo = o.fields()
+        fg = cav.fields_window(x0, y0, w, h)
+        m = np.ones((h, w), bool)
+        d = steps + 2
+        if x0 > 0:
+            m[:, :d] = False
+        if x0 + w < n:
+            m[:, w - d:] = False
+        if y0 > 0:
+            m[:d, :] = False
+        if y0 + h < n:
+            m[h - d:, :] = False
+        assert m.sum() > 100
+        for key, tol in (("T", 1e-5), ("C", 1e-5), ("ux", 1e-4), ("uy", 1e-4)):
+            a, b = fg[key][m], fo[key][m]
+            if key in ("T", "C"):
+                a, b = a - 0.5, b - 0.5
+            err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+            assert err <= tol, ((x0, y0), key, err)
+        # the Dirichlet walls carry their values on the wall nodes
+        if x0 == 0:
+            np.testing.assert_allclose(fg["T"][:, 0], 1.0, rtol=0, atol=1e-6)
+        if x0 + w == n:
+            np.testing.assert_allclose(fg["T"][:, -1], 0.0, rtol=0, atol=1e-6)
+    cav.close()
