@@ -50,7 +50,9 @@ __device__ __forceinline__ R wall_momentum(const Coef<R>& c, int side, int q) {
 // for 16-bit storage in the two-buffer layout, whose kernels are issue-bound: it
 // saves ~10 % there (GB300, 4096^2); the FP32 kernels are DRAM-bound and measured
 // 3 % (two-buffer) and 13 % (in-place) slower with it, so they keep one path.
-template <bool SWAP, bool WITH_F, typename S, typename R>
+// NC: load through the non-coherent path (the in-place odd step, whose threads each
+// write only the locations they have read themselves).
+template <bool SWAP, bool WITH_F, bool NC = false, typename S, typename R>
 __device__ __forceinline__ void gather_pull_inner(const S* __restrict__ buf, const Geom& G,
                                                   size_t self, R f[9], R g[5], R h[5]) {
     const S* p = buf + self;
@@ -59,15 +61,17 @@ __device__ __forceinline__ void gather_pull_inner(const S* __restrict__ buf, con
         for (int q = 0; q < 9; ++q) {
             const long long off = (long long)(QF + (SWAP ? opp_of(q) : q)) * (long long)G.plane -
                                   ex_of(q) - (long long)ey_of(q) * G.pitch;
-            f[q] = Store<S>::ld(p + off);
+            f[q] = NC ? Store<S>::ld_nc(p + off) : Store<S>::ld(p + off);
         }
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const long long d = -(long long)ex_of(q) - (long long)ey_of(q) * G.pitch;
         const int slot = SWAP ? opp_of(q) : q;
-        g[q] = Store<S>::ld(p + ((long long)(QG + slot) * (long long)G.plane + d));
-        h[q] = Store<S>::ld(p + ((long long)(QH + slot) * (long long)G.plane + d));
+        const S* pg = p + ((long long)(QG + slot) * (long long)G.plane + d);
+        const S* ph = p + ((long long)(QH + slot) * (long long)G.plane + d);
+        g[q] = NC ? Store<S>::ld_nc(pg) : Store<S>::ld(pg);
+        h[q] = NC ? Store<S>::ld_nc(ph) : Store<S>::ld(ph);
     }
 }
 
@@ -444,6 +448,81 @@ step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, G
         store_aa_odd<EXT>(buf, G, i, j, self, c, f, g, h, seed);
     else
         store_aa_even(buf, G, self, c, f, g, h, seed);
+    store_hist(hist, G, self, hv);
+}
+
+// The odd step split in two launches: the inner nodes (all eight neighbours in the
+// cavity) with no wall logic and uniform address offsets, and the ring of outermost
+// nodes with the general code.  Each thread reads and writes only its own set of
+// locations, so the two launches touch disjoint memory.  The odd step compiled as
+// one kernel needed 78 registers and 1.6x the even step's instructions.
+template <typename S, typename R>
+__device__ __forceinline__ void store_aa_odd_inner(S* __restrict__ buf, const Geom& G, size_t self,
+                                                   const Coef<R>& c, const R f[9], const R g[5],
+                                                   const R h[5], uint32_t& seed) {
+    const int sr = sr_node<S>(c.sr, f, g, h);
+    S* p = buf + self;
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+        put(p + ((long long)(QF + q) * (long long)G.plane + ex_of(q) + (long long)ey_of(q) * G.pitch),
+            f[q], sr, seed, q);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const long long d = (long long)ex_of(q) + (long long)ey_of(q) * G.pitch;
+        put(p + ((long long)(QG + q) * (long long)G.plane + d), g[q], sr, seed, QG + q);
+        put(p + ((long long)(QH + q) * (long long)G.plane + d), h[q], sr, seed, QH + q);
+    }
+}
+
+template <typename S, bool EXT>
+__global__ void __launch_bounds__(256)
+step_aa_odd_inner_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
+                         Coef<typename Real<S>::type> c) {
+    using R = typename Real<S>::type;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (!((unsigned)(i - 1) < (unsigned)(G.nx - 2) && (unsigned)(j - 1) < (unsigned)(G.ny - 2)))
+        return;
+    R f[9], g[5], h[5], hv[4];
+    const size_t self = (size_t)j * G.pitch + i;
+    gather_pull_inner<true, true, true>(buf, G, self, f, g, h);
+    load_hist(hist, G, self, hv);
+    uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
+    collide_node<EXT>(c, self, G.plane, f, g, h, hv);
+    store_aa_odd_inner(buf, G, self, c, f, g, h, seed);
+    store_hist(hist, G, self, hv);
+}
+
+// Node k of the outermost ring, k = 0 .. 2 nx + 2 (ny - 2) - 1: bottom row, top row,
+// left column, right column (rows 1 .. ny - 2).
+__device__ __forceinline__ void ring_node(const Geom& G, long long k, int& i, int& j) {
+    if (k < G.nx) {
+        i = (int)k; j = 0;
+    } else if (k < 2LL * G.nx) {
+        i = (int)(k - G.nx); j = G.ny - 1;
+    } else if (k < 2LL * G.nx + (G.ny - 2)) {
+        i = 0; j = (int)(k - 2LL * G.nx) + 1;
+    } else {
+        i = G.nx - 1; j = (int)(k - 2LL * G.nx - (G.ny - 2)) + 1;
+    }
+}
+
+template <typename S, bool EXT>
+__global__ void __launch_bounds__(128)
+step_aa_odd_ring_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
+                        Coef<typename Real<S>::type> c) {
+    using R = typename Real<S>::type;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2LL * G.nx + 2LL * (G.ny - 2)) return;
+    int i, j;
+    ring_node(G, k, i, j);
+    R f[9], g[5], h[5], hv[4];
+    const size_t self = (size_t)j * G.pitch + i;
+    gather_pull<true, true, EXT>(buf, G, i, j, c, f, g, h);
+    load_hist(hist, G, self, hv);
+    uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
+    collide_node<EXT>(c, self, G.plane, f, g, h, hv);
+    store_aa_odd<EXT>(buf, G, i, j, self, c, f, g, h, seed);
     store_hist(hist, G, self, hv);
 }
 

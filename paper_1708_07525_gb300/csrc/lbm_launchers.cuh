@@ -55,7 +55,21 @@ cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
     using R = typename Real<S>::type;
     dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
     const bool ext = c.poro || c.moving;
-    if (odd && ext)
+    if (odd && G.nx >= 3 && G.ny >= 3) {
+        // inner nodes without wall logic, then the ring of outermost nodes
+        if (ext)
+            step_aa_odd_inner_kernel<S, true><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+        else
+            step_aa_odd_inner_kernel<S, false><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const long long nring = 2LL * G.nx + 2LL * (G.ny - 2);
+        const unsigned nb = (unsigned)((nring + 127) / 128);
+        if (ext)
+            step_aa_odd_ring_kernel<S, true><<<nb, 128, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+        else
+            step_aa_odd_ring_kernel<S, false><<<nb, 128, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+    } else if (odd && ext)
         step_aa_kernel<S, true, true><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
     else if (odd)
         step_aa_kernel<S, true, false><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
