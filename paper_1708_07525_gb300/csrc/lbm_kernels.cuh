@@ -46,10 +46,11 @@ __device__ __forceinline__ R wall_momentum(const Coef<R>& c, int side, int q) {
 // moving-wall code is not compiled in (the fast path of the plain cavity).
 // Nodes whose eight neighbours all lie in the cavity (every node but the outermost
 // ring) can take a path with no wall rule, where each address is the node's own plus
-// an offset that is the same for every thread (kept in uniform registers).  Taken
-// for 16-bit storage in the two-buffer layout, whose kernels are issue-bound: it
-// saves ~10 % there (GB300, 4096^2); the FP32 kernels are DRAM-bound and measured
-// 3 % (two-buffer) and 13 % (in-place) slower with it, so they keep one path.
+// an offset that is the same for every thread (kept in uniform registers).  The
+// single-cavity kernels for the inner nodes call it directly (with the ring in a
+// launch of its own); inside gather_pull it is taken for 16-bit storage in the
+// two-buffer layout (the batch kernels), whose kernels are issue-bound.  Compiled
+// into the DRAM-bound FP32 kernels, either way, it measured slower (3-13 %).
 // NC: load through the non-coherent path (the in-place odd step, whose threads each
 // write only the locations they have read themselves).
 template <bool SWAP, bool WITH_F, bool NC = false, typename S, typename R>
@@ -355,6 +356,45 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
         return;
     R f[9], g[5], h[5], hv[4];
     const size_t self = (size_t)j * G.pitch + i;
+    if (INNER)
+        gather_pull_inner<false, true>(src, G, self, f, g, h);   // no wall logic compiled in
+    else
+        gather_pull<false, true, EXT>(src, G, i, j, c, f, g, h);
+    load_hist(hist, G, self, hv);
+    uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
+    collide_node<EXT>(c, self, G.plane, f, g, h, hv);
+    store_ab(dst, G, self, c, f, g, h, seed);
+    store_hist(hist, G, self, hv);
+}
+
+// Node k of the outermost ring, k = 0 .. 2 nx + 2 (ny - 2) - 1: bottom row, top row,
+// left column, right column (rows 1 .. ny - 2).
+__device__ __forceinline__ void ring_node(const Geom& G, long long k, int& i, int& j) {
+    if (k < G.nx) {
+        i = (int)k; j = 0;
+    } else if (k < 2LL * G.nx) {
+        i = (int)(k - G.nx); j = G.ny - 1;
+    } else if (k < 2LL * G.nx + (G.ny - 2)) {
+        i = 0; j = (int)(k - 2LL * G.nx) + 1;
+    } else {
+        i = G.nx - 1; j = (int)(k - 2LL * G.nx - (G.ny - 2)) + 1;
+    }
+}
+
+// The outermost ring of nodes of the two-buffer step with halfway walls (the inner
+// nodes run step_ab_kernel<S, EXT, true>): node k of the ring as in ring_node().
+template <typename S, bool EXT>
+__global__ void __launch_bounds__(128)
+step_ab_ring_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                    typename Real<S>::type* __restrict__ hist, Geom G,
+                    Coef<typename Real<S>::type> c) {
+    using R = typename Real<S>::type;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2LL * G.nx + 2LL * (G.ny - 2)) return;
+    int i, j;
+    ring_node(G, k, i, j);
+    R f[9], g[5], h[5], hv[4];
+    const size_t self = (size_t)j * G.pitch + i;
     gather_pull<false, true, EXT>(src, G, i, j, c, f, g, h);
     load_hist(hist, G, self, hv);
     uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
@@ -493,19 +533,6 @@ step_aa_odd_inner_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict
     store_hist(hist, G, self, hv);
 }
 
-// Node k of the outermost ring, k = 0 .. 2 nx + 2 (ny - 2) - 1: bottom row, top row,
-// left column, right column (rows 1 .. ny - 2).
-__device__ __forceinline__ void ring_node(const Geom& G, long long k, int& i, int& j) {
-    if (k < G.nx) {
-        i = (int)k; j = 0;
-    } else if (k < 2LL * G.nx) {
-        i = (int)(k - G.nx); j = G.ny - 1;
-    } else if (k < 2LL * G.nx + (G.ny - 2)) {
-        i = 0; j = (int)(k - 2LL * G.nx) + 1;
-    } else {
-        i = G.nx - 1; j = (int)(k - 2LL * G.nx - (G.ny - 2)) + 1;
-    }
-}
 
 template <typename S, bool EXT>
 __global__ void __launch_bounds__(128)
