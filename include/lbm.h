@@ -180,6 +180,13 @@ lbm_status lbm_derive_params_lid(lbm_grid grid, double Re, double Gr, double Da,
                                  double Pr, double Le, double N, double J, double sigma,
                                  double U0, double varpi, lbm_params* out);
 
+/* The lid-driven mapping of lbm_derive_params_lid() for walls with nodes on them
+ * (nee = 1, Sec. 3.3): L = nx - 1, nx, ny >= 5; corner nodes of the top wall move
+ * with the lid. */
+lbm_status lbm_derive_params_lid_nee(lbm_grid grid, double Re, double Gr, double Da, double eps,
+                                     double Pr, double Le, double N, double J, double sigma,
+                                     double U0, double varpi, lbm_params* out);
+
 /* Switch parameters from lbm_derive_params() to the coupled "model A" equilibria
  * (Eqs. 30-31) with the same effective diffusivities: by Eq. 32,
  * 1/zeta_a = 1/2 + alpha_e / (sigma c_sT^2), 1/eta_D = 1/2 + D_e / (eps c_sT^2).

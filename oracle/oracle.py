@@ -118,12 +118,14 @@ def derive(nx, ny, Ra, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, Ma=0.1, varpi=0.4,
     return p
 
 
-def derive_lid(nx, ny, Re, Gr, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, U0=0.1, varpi=0.4) -> Params:
+def derive_lid(nx, ny, Re, Gr, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, U0=0.1, varpi=0.4,
+               nee=False) -> Params:
     """Lid-driven porous cavity of Sec. 4.3: the top wall moves with U0 along +x, top
     T = C = 1, bottom T = C = 0, left/right adiabatic; Re = L U0 / nu with
-    1/s_nu = 1/2 + J L U0 / (c_s^2 Re); Gr = g beta_T dT L^3 / nu^2 (L = nx)."""
-    p = derive(nx, ny, 1e4, Da, eps, Pr, Le, N, J, sigma, 0.1, varpi)
-    L = float(nx)
+    1/s_nu = 1/2 + J L U0 / (c_s^2 Re); Gr = g beta_T dT L^3 / nu^2 (L = nx, or nx - 1
+    with nodes on the walls)."""
+    p = derive(nx, ny, 1e4, Da, eps, Pr, Le, N, J, sigma, 0.1, varpi, nee=nee)
+    L = float(nx - 1) if nee else float(nx)
     nu_e = J * L * U0 / Re
     p.nu_e, p.nu = nu_e, nu_e / J
     p.alpha_e = p.nu / Pr

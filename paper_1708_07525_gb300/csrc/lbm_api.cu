@@ -438,9 +438,11 @@ lbm_status lbm_derive_params_convective(int Nx, double Ra, double Da, double eps
     return LBM_OK;
 }
 
-lbm_status lbm_derive_params_lid(lbm_grid grid, double Re, double Gr, double Da, double eps,
-                                 double Pr, double Le, double N, double J, double sigma,
-                                 double U0, double varpi, lbm_params* out) {
+namespace {
+
+lbm_status derive_lid_core(lbm_grid grid, int nee, double Re, double Gr, double Da, double eps,
+                           double Pr, double Le, double N, double J, double sigma, double U0,
+                           double varpi, lbm_params* out) {
     if (!out || grid.nx < 3 || grid.ny < 3 || !(Re > 0.0) || !(Gr >= 0.0) || !(Da > 0.0) ||
         !(eps > 0.0 && eps <= 1.0) || !(Pr > 0.0) || !(Le > 0.0) || !(J > 0.0) || !(sigma > 0.0)) {
         set_global_error("lbm_derive_params_lid: invalid arguments");
@@ -449,10 +451,10 @@ lbm_status lbm_derive_params_lid(lbm_grid grid, double Re, double Gr, double Da,
     if (!(U0 > 0.0)) U0 = 0.1;
     if (!(varpi > 0.0)) varpi = 0.4;
     // reuse the cavity mapping for everything but the flow scales, then set those (Sec. 4.3)
-    lbm_status st = lbm_derive_params(grid, 1e4, Da, eps, Pr, Le, N, J, sigma, 0.1, varpi, out);
+    lbm_status st = derive_core(grid, nee, 1e4, Da, eps, Pr, Le, N, J, sigma, 0.1, varpi, out);
     if (st != LBM_OK) return st;
     lbm_params P = *out;
-    const double L = grid.nx, cs2 = 1.0 / 3.0, csT2 = 0.5 * varpi;
+    const double L = nee ? grid.nx - 1.0 : (double)grid.nx, cs2 = 1.0 / 3.0, csT2 = 0.5 * varpi;
     const double nu_e = J * L * U0 / Re;             // 1/s_nu = 1/2 + J L U0 / (c_s^2 Re)
     const double nu = nu_e / J;
     const double alpha_e = nu / Pr, D_e = alpha_e / Le;
@@ -477,6 +479,20 @@ lbm_status lbm_derive_params_lid(lbm_grid grid, double Re, double Gr, double Da,
     }
     *out = P;
     return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_derive_params_lid(lbm_grid grid, double Re, double Gr, double Da, double eps,
+                                 double Pr, double Le, double N, double J, double sigma,
+                                 double U0, double varpi, lbm_params* out) {
+    return derive_lid_core(grid, 0, Re, Gr, Da, eps, Pr, Le, N, J, sigma, U0, varpi, out);
+}
+
+lbm_status lbm_derive_params_lid_nee(lbm_grid grid, double Re, double Gr, double Da, double eps,
+                                     double Pr, double Le, double N, double J, double sigma,
+                                     double U0, double varpi, lbm_params* out) {
+    return derive_lid_core(grid, 1, Re, Gr, Da, eps, Pr, Le, N, J, sigma, U0, varpi, out);
 }
 
 lbm_status lbm_params_model_a(lbm_params* p) {

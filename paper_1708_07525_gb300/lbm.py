@@ -87,6 +87,7 @@ def lib():
             L.lbm_params_model_a.argtypes = [C.POINTER(lbm_params)]
             L.lbm_derive_params_lid.argtypes = [lbm_grid] + [C.c_double] * 11 + [C.POINTER(lbm_params)]
             L.lbm_derive_params_nee.argtypes = [lbm_grid] + [C.c_double] * 10 + [C.POINTER(lbm_params)]
+            L.lbm_derive_params_lid_nee.argtypes = [lbm_grid] + [C.c_double] * 11 + [C.POINTER(lbm_params)]
             L.lbm_derive_params_convective.argtypes = ([C.c_int] + [C.c_double] * 12
                                                        + [C.POINTER(lbm_params)])
             L.lbm_nusselt_sherwood_tb.argtypes = [P, dp]
@@ -109,6 +110,7 @@ def lib():
             L.lbm_last_error.restype = C.c_char_p
             for name in ("lbm_derive_params", "lbm_params_model_a", "lbm_derive_params_lid",
                          "lbm_derive_params_nee", "lbm_derive_params_convective",
+                         "lbm_derive_params_lid_nee",
                          "lbm_nusselt_sherwood_tb", "lbm_create", "lbm_create_raw",
                          "lbm_reset", "lbm_step",
                          "lbm_fields", "lbm_fields_window", "lbm_nusselt_sherwood", "lbm_residual",
@@ -190,6 +192,15 @@ def lbm_derive_params_convective(Nx, Ra, Da, eps, Pr, Le, N, BiT, BiC, J=1.0, si
     p = lbm_params()
     _check(lib().lbm_derive_params_convective(int(Nx), Ra, Da, eps, Pr, Le, N, BiT, BiC, J, sigma,
                                               Ma, varpi, C.byref(p)))
+    return p
+
+
+def lbm_derive_params_lid_nee(nx, ny, Re, Gr, Da, eps, Pr, Le, N, J=1.0, sigma=1.0, U0=0.1,
+                              varpi=0.0):
+    """lbm_derive_params_lid for walls with nodes on them (Sec. 3.3), L = nx - 1."""
+    p = lbm_params()
+    _check(lib().lbm_derive_params_lid_nee(lbm_grid(int(nx), int(ny)), Re, Gr, Da, eps, Pr, Le, N,
+                                           J, sigma, U0, varpi, C.byref(p)))
     return p
 
 

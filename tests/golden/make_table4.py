@@ -4,7 +4,10 @@ Da = 0.1, Pr = 1, Le = 1, U0 = 0.1) for several buoyancy ratios N, each run unti
 the mean Nu and Sh of the bottom wall change by less than 1e-7 (relative) over
 20,000 steps.  Table 4 of the paper prints Nu = Sh at the bottom wall.
 
-Usage: python tests/golden/make_table4.py [N values, comma separated]
+With --nee the same cavity is run with the paper's own walls (Sec. 3.3: 129 x 129 nodes
+on the walls, L = 128) into tests/golden/table4_nee_oracle.json.
+
+Usage: python tests/golden/make_table4.py [N values, comma separated] [--nee]
 """
 import json
 import multiprocessing as mp
@@ -21,11 +24,13 @@ sys.path.insert(0, ROOT)
 ARGS = dict(nx=128, ny=128, Re=100.0, Gr=1e2, Da=0.1, eps=0.95, Pr=1.0, Le=1.0)
 
 
-def run(N):
+def run(job):
+    N, nee = job
     from oracle import oracle as O
     O.set_threads(1)
-    p = O.derive_lid(ARGS["nx"], ARGS["ny"], ARGS["Re"], ARGS["Gr"], ARGS["Da"], ARGS["eps"],
-                     ARGS["Pr"], ARGS["Le"], N)
+    n = 1 if nee else 0
+    p = O.derive_lid(ARGS["nx"] + n, ARGS["ny"] + n, ARGS["Re"], ARGS["Gr"], ARGS["Da"],
+                     ARGS["eps"], ARGS["Pr"], ARGS["Le"], N, nee=nee)
     o = O.Oracle(p, seed=11, noise=1e-3)
     prev = None
     t0 = time.time()
@@ -43,15 +48,19 @@ def run(N):
 
 
 def main():
-    Ns = [float(x) for x in sys.argv[1].split(",")] if len(sys.argv) > 1 else \
+    nee = "--nee" in sys.argv
+    args = [a for a in sys.argv[1:] if a != "--nee"]
+    Ns = [float(x) for x in args[0].split(",")] if args else \
         [-1500.0, -500.0, -100.0, 100.0, 500.0]
     with mp.get_context("spawn").Pool(len(Ns)) as pool:
-        rows = pool.map(run, Ns)
+        rows = pool.map(run, [(N, nee) for N in Ns])
     out = {"source": "oracle/ (FP64 CPU), tests/golden/make_table4.py",
            "case": "Sec. 4.3 lid-driven porous cavity, 128 x 128, Gr 1e2, eps 0.95, Re 100, "
-                   "Da 0.1, Pr 1, Le 1, U0 0.1, seed 11",
+                   "Da 0.1, Pr 1, Le 1, U0 0.1, seed 11"
+                   + (", walls on nodes (129 x 129 nodes, Sec. 3.3)" if nee else ", halfway walls"),
            "rows": rows}
-    with open(os.path.join(HERE, "table4_oracle.json"), "w") as f:
+    name = "table4_nee_oracle.json" if nee else "table4_oracle.json"
+    with open(os.path.join(HERE, name), "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps(out))
 

@@ -105,3 +105,16 @@ def test_nee_misuse_rejected():
     assert ei.value.status == lbm.ERR_INVALID
     with pytest.raises(lbm.LbmError):
         lbm.lbm_derive_params_nee(4, 16, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
+
+
+def test_derive_lid_nee_matches_the_oracle(oracle_mod):
+    g = lbm.lbm_derive_params_lid_nee(129, 129, 100.0, 1e2, 0.1, 0.95, 1.0, 1.0, -500.0)
+    o = oracle_mod.derive_lid(129, 129, 100.0, 1e2, 0.1, 0.95, 1.0, 1.0, -500.0, nee=True)
+    assert g.nee == 1 and o.nee == 1
+    for k in ("nu", "K", "gbT", "gbC", "T0", "C0"):
+        assert abs(getattr(g, k) - getattr(o, k)) <= 1e-15 * max(1.0, abs(getattr(o, k))), k
+    for k in ("s", "zeta", "eta", "Tw", "Cw"):
+        np.testing.assert_allclose(list(getattr(g, k)), list(getattr(o, k)), rtol=1e-15, atol=0)
+    assert g.uw[3][0] == o.uw[3][0] == 0.1
+    # L = 128 spacings: Re = L U0 / nu, K = Da L^2
+    assert abs(g.nu - 128 * 0.1 / 100.0) < 1e-15 and abs(g.K - 0.1 * 128 * 128) < 1e-9

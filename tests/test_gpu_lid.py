@@ -74,3 +74,23 @@ def test_table4_bottom_wall_nusselt():
         assert abs(ns[0] - ref) <= 0.02 * ref and abs(ns[1] - ref) <= 0.02 * ref
         assert abs(ns[0] - ns[1]) <= 1e-6 * ns[0]       # Le = 1: Nu = Sh
         c.close()
+
+
+@pytest.mark.parametrize("nsteps", [1, 1000])
+def test_lid_cavity_with_wall_nodes_f64_against_oracle(oracle_mod, nsteps):
+    """The paper's own walls (Sec. 3.3) on the lid-driven cavity: the moving lid enters
+    Eq. 33 as u_w (the top corners move with it)."""
+    O = oracle_mod
+    p = lbm.lbm_derive_params_lid_nee(33, 29, 100.0, 1e2, 0.1, 0.95, 1.0, 1.0, -500.0)
+    po = O.derive_lid(33, 29, 100.0, 1e2, 0.1, 0.95, 1.0, 1.0, -500.0, nee=True)
+    gpu = lbm.Cavity(params=p, precision="f64", seed=4, noise=0.02)
+    ora = O.Oracle(po, seed=4, noise=0.02)
+    gpu.step(nsteps)
+    ora.step(nsteps)
+    fg, fo = gpu.fields(), ora.fields()
+    for k in KEYS:
+        if k in ("ux", "uy") and np.abs(fg[k] - fo[k]).max() < 1e-15:
+            continue
+        assert rel_l2(fg[k], fo[k]) <= 1e-12, k
+    np.testing.assert_allclose(gpu.nusselt_sherwood_tb(), ora.nusselt_sherwood_tb(), rtol=1e-11)
+    gpu.close()
