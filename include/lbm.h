@@ -10,18 +10,20 @@
  * plus four history values per node (T u, C u at the previous step) for the
  * explicit time derivative in the source terms of Eq. 27.
  *
- * One time step = one fused kernel launch: pull-streaming (Eq. 11) with the
- * halfway wall rules, macroscopic fields (Eqs. 16, 18-19, 26), total force
- * (Eqs. 5-6), the D2Q9 collision in moment space (Eq. 10 with Eqs. 12-15) and
- * the two D2Q5 collisions (Eqs. 21-22 with Eqs. 24-25, 27).
+ * One time step = one fused pass over the nodes (one kernel launch, or two
+ * where the outermost ring of nodes has a launch of its own): pull-streaming
+ * (Eq. 11) with the wall rules, macroscopic fields (Eqs. 16, 18-19, 26), total
+ * force (Eqs. 5-6), the D2Q9 collision in moment space (Eq. 10 with Eqs.
+ * 12-15) and the two D2Q5 collisions (Eqs. 21-22 with Eqs. 24-25, 27).
  *
- * Cavity: nodes (i, j), 0 <= i < nx, 0 <= j < ny, at positions (i+1/2, j+1/2);
- * walls at x = 0, x = nx, y = 0, y = ny, halfway between the outermost nodes
- * and their missing neighbours.  Left wall T = C = 1, right wall T = C = 0,
- * top and bottom adiabatic and impermeable, all walls no-slip.  The paper's
- * own walls are node-based non-equilibrium extrapolation (Sec. 3.3); this
- * library implements halfway bounce-back (f), anti-bounce-back (Dirichlet g,
- * h) and bounce-back (adiabatic g, h).
+ * Cavity (default walls): nodes (i, j), 0 <= i < nx, 0 <= j < ny, at positions
+ * (i+1/2, j+1/2); walls at x = 0, x = nx, y = 0, y = ny, halfway between the
+ * outermost nodes and their missing neighbours.  Left wall T = C = 1, right
+ * wall T = C = 0, top and bottom adiabatic and impermeable, all walls no-slip:
+ * halfway bounce-back (f), anti-bounce-back (Dirichlet g, h) and bounce-back
+ * (adiabatic g, h).  With lbm_params.nee = 1 the outermost nodes lie on the
+ * walls instead and follow the paper's own scheme (Sec. 3.3, Eqs. 33-37),
+ * with convective walls (Eq. 39) available.
  *
  * Conventions for every entry point:
  *   - Returns an lbm_status; never aborts, exits or traps.  The message of the
