@@ -94,8 +94,10 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
 // The same step for tiles of exactly BATCH_THREADS nodes: one node per thread,
 // one tile per CTA and no loop, so nothing loop-invariant is hoisted into
 // registers (the descriptor stays in shared memory and occupancy stays high).
+// The two-buffer variant fits 64 registers without spilling (8 CTAs per SM
+// instead of 7); the in-place one would spill there and keeps its count.
 template <typename S, bool AA>
-__global__ void __launch_bounds__(BATCH_THREADS)
+__global__ void __launch_bounds__(BATCH_THREADS, AA ? 1 : 8)
 batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
                    const int* __restrict__ tile_owner, int tile_begin, int parity) {
     using R = typename Real<S>::type;
