@@ -94,3 +94,18 @@ def test_lid_cavity_with_wall_nodes_f64_against_oracle(oracle_mod, nsteps):
         assert rel_l2(fg[k], fo[k]) <= 1e-12, k
     np.testing.assert_allclose(gpu.nusselt_sherwood_tb(), ora.nusselt_sherwood_tb(), rtol=1e-11)
     gpu.close()
+
+
+def test_table5_gpu_reproduces_stored_oracle():
+    """Table 5 (eps = 0.6, the paper's model and model A): the GPU FP64 run to the oracle's
+    step count reproduces the stored bottom- and top-wall Nu, Sh (1e-9)."""
+    gold = json.load(open(os.path.join(GOLD, "table5_oracle.json")))
+    for row in gold["rows"]:
+        p = lbm.lbm_derive_params_lid(128, 128, 100.0, 1e2, 0.1, 0.6, 1.0, 1.0, row["N"])
+        if row["model_a"]:
+            lbm.lbm_params_model_a(p)
+        c = lbm.Cavity(params=p, precision="f64", seed=11, noise=1e-3)
+        c.step(row["steps"])
+        np.testing.assert_allclose(c.nusselt_sherwood_tb(), [row["nu_bottom"], row["sh_bottom"],
+                                                             row["nu_top"], row["sh_top"]], rtol=1e-9)
+        c.close()
