@@ -109,3 +109,16 @@ def test_table5_gpu_reproduces_stored_oracle():
         np.testing.assert_allclose(c.nusselt_sherwood_tb(), [row["nu_bottom"], row["sh_bottom"],
                                                              row["nu_top"], row["sh_top"]], rtol=1e-9)
         c.close()
+
+
+def test_table4_with_the_papers_walls_gpu_reproduces_stored_oracle():
+    """Table 4's cavity with the paper's own walls (129 x 129 wall nodes): the GPU FP64 run
+    to the oracle's step count reproduces the stored Nu, Sh of both walls (1e-9)."""
+    gold = json.load(open(os.path.join(GOLD, "table4_nee_oracle.json")))
+    for row in gold["rows"][:2]:
+        p = lbm.lbm_derive_params_lid_nee(129, 129, 100.0, 1e2, 0.1, 0.95, 1.0, 1.0, row["N"])
+        c = lbm.Cavity(params=p, precision="f64", seed=11, noise=1e-3)
+        c.step(row["steps"])
+        np.testing.assert_allclose(c.nusselt_sherwood_tb(), [row["nu_bottom"], row["sh_bottom"],
+                                                             row["nu_top"], row["sh_top"]], rtol=1e-9)
+        c.close()
