@@ -938,7 +938,7 @@ lbm_status lbm_save(lbm_ctx* c, void* buf, size_t* len) {
     CkptHeader h;
     std::memset(&h, 0, sizeof h);
     std::memcpy(h.magic, "LBMDDC1", 8);
-    h.version = 1;
+    h.version = 2;   // 2: lbm_params carries the wall-node fields (nee, BiT, BiC)
     h.nx = c->G.nx;
     h.ny = c->G.ny;
     h.prec = c->prec;
@@ -966,8 +966,12 @@ lbm_status lbm_load(lbm_ctx* c, const void* buf, size_t len) {
     CkptHeader h;
     if (len < sizeof h) return c->fail(LBM_ERR_INVALID, "lbm_load: truncated checkpoint");
     std::memcpy(&h, buf, sizeof h);
-    if (std::memcmp(h.magic, "LBMDDC1", 8) != 0 || h.version != 1)
-        return c->fail(LBM_ERR_INVALID, "lbm_load: not a checkpoint of this library");
+    if (std::memcmp(h.magic, "LBMDDC1", 8) != 0 || h.version != 2)
+        return c->fail(LBM_ERR_INVALID, "lbm_load: not a checkpoint of this library version");
+    if (const char* bad = check_params(h.P))
+        return c->fail(LBM_ERR_INVALID, "lbm_load: checkpoint parameters: %s", bad);
+    if (h.P.nee && c->layout != LBM_AB_PULL)
+        return c->fail(LBM_ERR_INVALID, "lbm_load: walls with nodes on them need the two-buffer layout");
     if (h.nx != c->G.nx || h.ny != c->G.ny || h.prec != c->prec || h.layout != c->layout ||
         h.pitch != c->G.pitch || len < need)
         return c->fail(LBM_ERR_INVALID, "lbm_load: checkpoint does not match this context");

@@ -337,6 +337,9 @@ class Cavity:
     def load(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         _check(lib().lbm_load(self.h, buf, len(blob)), self.h)
+        p = lbm_params()                      # the checkpoint brings its own parameters
+        _check(lib().lbm_get_params(self.h, C.byref(p)), self.h)
+        self.params = p
 
     def device_bytes(self) -> int:
         return int(lib().lbm_device_bytes(self.h))

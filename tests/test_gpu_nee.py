@@ -223,3 +223,27 @@ def test_convective_cavity_16bit_storage(oracle_mod, precision):
         assert rel_l2(fg[k], fo[k]) <= 2e-2, (k, rel_l2(fg[k], fo[k]))
     assert np.isfinite(gpu.nusselt_sherwood()).all()
     gpu.close()
+
+
+def test_checkpoint_resume_with_wall_nodes_bitwise():
+    """A checkpoint carries the wall-node parameters (nee, Biot numbers): a plain cavity
+    of the same grid that loads it resumes bit for bit; an in-place context refuses it."""
+    p = lbm.lbm_derive_params_convective(36, 1e4, 1e-2, 0.6, 1.0, 1.0, 1.0, 1.0, 200.0)
+    a = lbm.Cavity(params=p, precision="f32", seed=3, noise=0.02)
+    a.step(333)
+    blob = a.save()
+    a.step(400)
+    b = lbm.Cavity(37, 37, 1e4, 1e-2, 0.6, 1.0, 1.0, 1.0, precision="f32", seed=99)
+    b.load(blob)
+    assert b.t == 333 and b.params.nee == 1 and b.params.BiC[1] == 200.0
+    b.step(400)
+    fa, fb = a.fields(), b.fields()
+    for k in KEYS:
+        assert np.array_equal(fa[k], fb[k]), k
+    np.testing.assert_array_equal(a.nusselt_sherwood(), b.nusselt_sherwood())
+    c = lbm.Cavity(37, 37, 1e4, 1e-2, 0.6, 1.0, 1.0, 1.0, precision="f32", layout="aa")
+    with pytest.raises(lbm.LbmError) as ei:
+        c.load(blob)
+    assert ei.value.status == lbm.ERR_INVALID
+    for x in (a, b, c):
+        x.close()
