@@ -68,6 +68,13 @@ Coef<R> make_coef(const lbm_params& P) {
     c.s5 = (R)P.s[5]; c.s6 = (R)P.s[6]; c.s7 = (R)P.s[7]; c.s8 = (R)P.s[8];
     c.za1 = (R)P.zeta[1]; c.za2 = (R)P.zeta[2]; c.za3 = (R)P.zeta[3]; c.za4 = (R)P.zeta[4];
     c.ed1 = (R)P.eta[1]; c.ed2 = (R)P.eta[2]; c.ed3 = (R)P.eta[3]; c.ed4 = (R)P.eta[4];
+    // 1 - s/2 factors of the forcing / source terms (Eqs. 10, 21, 22), in the compute precision
+    c.h1 = (R)(1.0 - 0.5 * P.s[1]); c.h2 = (R)(1.0 - 0.5 * P.s[2]);
+    c.h3 = (R)(1.0 - 0.5 * P.s[3]); c.h4 = (R)(1.0 - 0.5 * P.s[4]);
+    c.h5 = (R)(1.0 - 0.5 * P.s[5]); c.h6 = (R)(1.0 - 0.5 * P.s[6]);
+    c.h7 = (R)(1.0 - 0.5 * P.s[7]); c.h8 = (R)(1.0 - 0.5 * P.s[8]);
+    c.hz1 = (R)(1.0 - 0.5 * P.zeta[1]); c.hz2 = (R)(1.0 - 0.5 * P.zeta[2]);
+    c.he1 = (R)(1.0 - 0.5 * P.eta[1]); c.he2 = (R)(1.0 - 0.5 * P.eta[2]);
     // Eqs. 24 / 25 (model A: Eqs. 30 / 31): n_eq,3 = c3 Phi
     c.c3T = (R)(P.model_a ? (5.0 * P.varpi - 4.0) * P.sigma : 5.0 * P.varpi - 4.0 * P.sigma);
     c.c3C = (R)(P.model_a ? (5.0 * P.varpi - 4.0) * eps : 5.0 * P.varpi - 4.0 * eps);

@@ -174,8 +174,10 @@ struct Coef {
     R l0, l0sq, l1;            // Eq. 19
     R drag_lin, drag_quad;     // eps nu / K and eps F_eps / sqrt(K) (Eq. 5)
     R s1, s2, s3, s4, s5, s6, s7, s8;   // Lambda (s_rho plays no role: m_0 is conserved)
+    R h1, h2, h3, h4, h5, h6, h7, h8;   // 1 - s_k / 2, the factors of the forcing (Eq. 10)
     R za1, za2, za3, za4;      // Theta (zeta_0 plays no role)
     R ed1, ed2, ed3, ed4;      // Q
+    R hz1, hz2, he1, he2;      // 1 - zeta_k / 2, 1 - eta_k / 2 (source terms of Eqs. 21-22)
     R c3T, c3C;                // 5 varpi - 4 sigma, 5 varpi - 4 eps (Eqs. 24, 25)
     // Per wall side (0 left, 1 right, 2 bottom, 3 top): 2 w~ (Phi_w - Phi0) with
     // w~ = varpi / 4, the anti-bounce-back constant in deviations.
@@ -243,7 +245,8 @@ __device__ __forceinline__ Macro<R> macro(const Coef<R>& c, const R f[9], const 
     R vy = jy + c.half_eps * Gy;
     R vm = sqrt_(vx * vx + vy * vy);
     R den = c.l0 + sqrt_(c.l0sq + c.l1 * vm);                       // Eq. 18
-    R ux = vx / den, uy = vy / den;
+    const R inv_den = R(1) / den;
+    R ux = vx * inv_den, uy = vy * inv_den;
     R um = sqrt_(ux * ux + uy * uy);
     R drag = c.drag_lin + c.drag_quad * um;                          // Eq. 5
     o.rho = rho;
@@ -264,13 +267,13 @@ __device__ __forceinline__ Macro<R> macro(const Coef<R>& c, const R f[9], const 
 // Pp = Phi - Phi0, P = Phi (Phi = T or C), c3 = 5 varpi - 4 cap.
 template <typename R>
 __device__ __forceinline__ void collide_d2q5(R d[5], R Pp, R P, R ux, R uy, R Xx, R Xy,
-                                             R r1, R r2, R r3, R r4, R c3) {
+                                             R r1, R r2, R r3, R r4, R c3, R q1, R q2) {
     const R n1 = d[1] - d[3];
     const R n2 = d[2] - d[4];
     const R n3 = ((d[1] + d[2]) + (d[3] + d[4])) - R(4) * d[0];
     const R n4 = (d[1] - d[2]) + (d[3] - d[4]);
-    const R k1 = r1 * (n1 - ux * P) - (R(1) - R(0.5) * r1) * Xx;
-    const R k2 = r2 * (n2 - uy * P) - (R(1) - R(0.5) * r2) * Xy;
+    const R k1 = r1 * (n1 - ux * P) - q1 * Xx;   // q_k = 1 - r_k / 2
+    const R k2 = r2 * (n2 - uy * P) - q2 * Xy;
     const R k3 = r3 * (n3 - c3 * Pp);
     const R k4 = r4 * n4;
     const R b1 = k1 * R(0.5), b2 = k2 * R(0.5), b3 = k3 * R(0.05), b4 = k4 * R(0.25);
@@ -312,14 +315,14 @@ __device__ __forceinline__ void collide(const Coef<R>& c, R f[9], R g[5], R h[5]
     const R S7 = R(2) * (ux * Fx - uy * Fy) * ie;
     const R S8 = (ux * Fy + uy * Fx) * ie;
     // Lambda (m - m_eq) - (I - Lambda/2) S, component by component (S_2 = -S_1, S_4 = -F_x, ...)
-    const R d1 = c.s1 * (m1 - e1) - (R(1) - R(0.5) * c.s1) * S1;
-    const R d2 = c.s2 * (m2 - e2) + (R(1) - R(0.5) * c.s2) * S1;
-    const R d3 = c.s3 * (m3 - ux) - (R(1) - R(0.5) * c.s3) * Fx;
-    const R d4 = c.s4 * (m4 + ux) + (R(1) - R(0.5) * c.s4) * Fx;
-    const R d5 = c.s5 * (m5 - uy) - (R(1) - R(0.5) * c.s5) * Fy;
-    const R d6 = c.s6 * (m6 + uy) + (R(1) - R(0.5) * c.s6) * Fy;
-    const R d7 = c.s7 * (m7 - e7) - (R(1) - R(0.5) * c.s7) * S7;
-    const R d8 = c.s8 * (m8 - e8) - (R(1) - R(0.5) * c.s8) * S8;
+    const R d1 = c.s1 * (m1 - e1) - c.h1 * S1;
+    const R d2 = c.s2 * (m2 - e2) + c.h2 * S1;
+    const R d3 = c.s3 * (m3 - ux) - c.h3 * Fx;
+    const R d4 = c.s4 * (m4 + ux) + c.h4 * Fx;
+    const R d5 = c.s5 * (m5 - uy) - c.h5 * Fy;
+    const R d6 = c.s6 * (m6 + uy) + c.h6 * Fy;
+    const R d7 = c.s7 * (m7 - e7) - c.h7 * S7;
+    const R d8 = c.s8 * (m8 - e8) - c.h8 * S8;
     // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
     const R a1 = d1 * R(1.0 / 36.0), a2 = d2 * R(1.0 / 36.0);
     const R a3 = d3 * R(1.0 / 6.0), a4 = d4 * R(1.0 / 12.0);
@@ -346,8 +349,8 @@ __device__ __forceinline__ void collide(const Coef<R>& c, R f[9], R g[5], R h[5]
     hist[1] = Tuy;
     hist[2] = Cux;
     hist[3] = Cuy;
-    collide_d2q5(g, M.Tp, T, ux, uy, XTx, XTy, c.za1, c.za2, c.za3, c.za4, c.c3T);
-    collide_d2q5(h, M.Cp, C, ux, uy, XCx, XCy, c.ed1, c.ed2, c.ed3, c.ed4, c.c3C);
+    collide_d2q5(g, M.Tp, T, ux, uy, XTx, XTy, c.za1, c.za2, c.za3, c.za4, c.c3T, c.hz1, c.hz2);
+    collide_d2q5(h, M.Cp, C, ux, uy, XCx, XCy, c.ed1, c.ed2, c.ed3, c.ed4, c.c3C, c.he1, c.he2);
 }
 
 // ---- SplitMix64 (Steele, Lea & Flood 2014): k-th output of a generator seeded with s
