@@ -174,6 +174,8 @@ struct lbm_ctx {
     int64_t t = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t aux = nullptr;           // second stream for the ring launches of split steps
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     Coef<double> cd{};
     Coef<float> cf{};
@@ -607,6 +609,18 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
     c->L.bx = bx;
     c->L.by = by;
     c->L.stream = c->stream;
+    c->L.aux = nullptr;
+    // a second stream lets the small ring launch of a split step run beside the inner one;
+    // without it both go to the context's stream
+    if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess) {
+        c->L.aux = c->aux;
+        c->L.fork = c->ev_fork;
+        c->L.join = c->ev_join;
+    } else {
+        cudaGetLastError();
+    }
     c->graph_chunk = O.graph_chunk == 0 ? 64 : (O.graph_chunk < 0 ? 0 : O.graph_chunk);
     if (c->graph_chunk & 1) c->graph_chunk += 1;   // a chunk must return to the same parity
     if (c->stream == nullptr || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread)
@@ -1032,6 +1046,9 @@ void lbm_destroy(lbm_ctx* c) {
     c->dfree(c->d_partial, (size_t)RES_SLOTS * 9 * sizeof(double));
     c->dfree(c->d_stage, 2 * c->nodes() * sizeof(double));
     c->dfree(c->poro, 2 * c->G.plane * c->rsz);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->aux) cudaStreamDestroy(c->aux);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -41,7 +41,30 @@ constexpr int RES_THREADS = 256;
 struct LaunchCfg {
     int bx, by;
     cudaStream_t stream;
+    // Optional second stream with two events: where a step is an inner-node launch plus
+    // a small launch for the outermost ring, the ring runs on `aux` beside the inner
+    // launch (the two write disjoint locations), joined back before the next step.
+    // aux == nullptr: both launches go to `stream`.
+    cudaStream_t aux;
+    cudaEvent_t fork, join;
 };
+
+// Stream for the ring launch of a split step (after forking from L.stream).
+inline cudaError_t ring_fork(const LaunchCfg& L, cudaStream_t* rs) {
+    *rs = L.stream;
+    if (!L.aux) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(L.fork, L.stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(L.aux, L.fork, 0);
+    if (e == cudaSuccess) *rs = L.aux;
+    return e;
+}
+// Makes L.stream wait for the ring launch.
+inline cudaError_t ring_join(const LaunchCfg& L) {
+    if (!L.aux) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(L.join, L.aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(L.stream, L.join, 0);
+    return e;
+}
 
 // Launchers, explicitly instantiated for S = double, float, __nv_bfloat16, __half.
 template <typename S>

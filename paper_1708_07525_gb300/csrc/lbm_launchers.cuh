@@ -34,33 +34,41 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
     using R = typename Real<S>::type;
     dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
     if (c.nee) {
-        // inner nodes: the plain pull; the ring of wall nodes: the rebuild (Sec. 3.3)
+        // the ring of wall nodes: the rebuild (Sec. 3.3); inner nodes: the plain pull
+        cudaStream_t rs;
+        cudaError_t e = ring_fork(L, &rs);
+        if (e != cudaSuccess) return e;
+        const long long nring = 2LL * G.nx + 2LL * (G.ny - 2);
+        nee_ring_kernel<S><<<(unsigned)((nring + 127) / 128), 128, 0, rs>>>(
+            (const S*)src, (S*)dst, (R*)hist, G, c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (c.poro)
             step_ab_kernel<S, true, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
         else
             step_ab_kernel<S, false, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        const long long nring = 2LL * G.nx + 2LL * (G.ny - 2);
-        nee_ring_kernel<S><<<(unsigned)((nring + 127) / 128), 128, 0, L.stream>>>(
-            (const S*)src, (S*)dst, (R*)hist, G, c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return ring_join(L);
     } else if (!std::is_same<S, float>::value && G.nx >= 3 && G.ny >= 3) {
         // inner nodes with no wall logic, then the ring of outermost nodes.  GB300, 4096^2:
         // BF16 385 -> 377 us, FP16 442 -> 410 us, FP64 (2048^2) 2201 -> 2148 us; the
         // DRAM-bound FP32 step measured slower split (446 -> 460 us) and stays one kernel.
         const bool ext = c.poro || c.moving;
-        if (ext)
-            step_ab_kernel<S, true, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
-        else
-            step_ab_kernel<S, false, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
-        cudaError_t e = cudaGetLastError();
+        cudaStream_t rs;
+        cudaError_t e = ring_fork(L, &rs);
         if (e != cudaSuccess) return e;
         const long long nring = 2LL * G.nx + 2LL * (G.ny - 2);
         const unsigned nb = (unsigned)((nring + 127) / 128);
         if (ext)
-            step_ab_ring_kernel<S, true><<<nb, 128, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+            step_ab_ring_kernel<S, true><<<nb, 128, 0, rs>>>((const S*)src, (S*)dst, (R*)hist, G, c);
         else
-            step_ab_ring_kernel<S, false><<<nb, 128, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+            step_ab_ring_kernel<S, false><<<nb, 128, 0, rs>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (ext)
+            step_ab_kernel<S, true, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+        else
+            step_ab_kernel<S, false, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return ring_join(L);
     } else if (c.poro || c.moving)
         step_ab_kernel<S, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
     else
@@ -75,19 +83,24 @@ cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
     dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
     const bool ext = c.poro || c.moving;
     if (odd && G.nx >= 3 && G.ny >= 3) {
-        // inner nodes without wall logic, then the ring of outermost nodes
-        if (ext)
-            step_aa_odd_inner_kernel<S, true><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
-        else
-            step_aa_odd_inner_kernel<S, false><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
-        cudaError_t e = cudaGetLastError();
+        // the ring of outermost nodes beside the inner nodes (no wall logic); the two
+        // launches touch disjoint locations
+        cudaStream_t rs;
+        cudaError_t e = ring_fork(L, &rs);
         if (e != cudaSuccess) return e;
         const long long nring = 2LL * G.nx + 2LL * (G.ny - 2);
         const unsigned nb = (unsigned)((nring + 127) / 128);
         if (ext)
-            step_aa_odd_ring_kernel<S, true><<<nb, 128, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+            step_aa_odd_ring_kernel<S, true><<<nb, 128, 0, rs>>>((S*)buf, (R*)hist, G, c);
         else
-            step_aa_odd_ring_kernel<S, false><<<nb, 128, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+            step_aa_odd_ring_kernel<S, false><<<nb, 128, 0, rs>>>((S*)buf, (R*)hist, G, c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (ext)
+            step_aa_odd_inner_kernel<S, true><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+        else
+            step_aa_odd_inner_kernel<S, false><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return ring_join(L);
     } else if (odd && ext)
         step_aa_kernel<S, true, true><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
     else if (odd)
