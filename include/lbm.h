@@ -279,7 +279,9 @@ size_t lbm_device_bytes(const lbm_ctx* ctx);
  * in CUDA graphs.  All cavities of a batch share the storage precision and the
  * memory pattern given in lbm_options; the per-cavity noise seed and amplitude
  * come from the descriptors.  Results of a cavity do not depend on the other
- * members of the batch (bitwise). */
+ * members of the batch (bitwise).  Cavities with wall nodes (lbm_params.nee,
+ * Sec. 3.3, convective walls included) may join two-buffer batches; moving
+ * walls and porosity fields are single-cavity features. */
 typedef struct lbm_batch lbm_batch;
 
 typedef struct {

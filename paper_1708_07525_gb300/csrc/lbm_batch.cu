@@ -143,10 +143,15 @@ bool params_ok(const lbm_params& P, std::string* why) {
     for (int s = 0; s < 4; ++s)
         if (P.uw[s][0] != 0.0 || P.uw[s][1] != 0.0)
             return bad("moving walls are not supported in batches (use a single cavity)");
-    if (P.nee) return bad("walls with nodes on them (nee) are not supported in batches");
-    for (int s = 0; s < 4; ++s)
-        if (P.BiT[s] != 0.0 || P.BiC[s] != 0.0)
-            return bad("convective walls are not supported in batches");
+    if (P.nee != 0 && P.nee != 1) return bad("nee must be 0 or 1");
+    if (P.nee && (P.nx < 5 || P.ny < 5)) return bad("walls with nodes on them need nx, ny >= 5");
+    for (int s = 0; s < 4; ++s) {
+        if (!(P.BiT[s] >= 0.0) || !(P.BiC[s] >= 0.0) || !std::isfinite(P.BiT[s]) ||
+            !std::isfinite(P.BiC[s]))
+            return bad("Biot numbers must be finite and >= 0");
+        if (!P.nee && (P.BiT[s] != 0.0 || P.BiC[s] != 0.0))
+            return bad("convective (Robin) walls need walls with nodes on them (nee = 1)");
+    }
     if (P.nx < 3 || P.ny < 3) return bad("nx and ny must be >= 3");
     if (!(P.eps > 0.0 && P.eps <= 1.0)) return bad("eps must lie in (0, 1]");
     if (!(P.sigma > 0.0) || !(P.K > 0.0)) return bad("sigma and K must be positive");
@@ -183,6 +188,7 @@ struct lbm_batch {
     std::vector<int> h_owner, h_ntiles;
     int total_tiles = 0;
     bool one_node_tiles = false;         // every tile has BATCH_THREADS nodes
+    bool has_nee = false;                // some cavity has wall nodes (Sec. 3.3)
     // L2 temporal blocking: groups of cavities whose working set fits in a share of
     // L2 are advanced `tblock` steps each before the next group is touched.
     std::vector<std::pair<int, int>> groups;   // [tile_begin, tile_end)
@@ -253,7 +259,7 @@ struct lbm_batch {
     int parity() const { return (int)(t & 1); }
     int mode_of(const Slot& s) const {
         const int odd = (int)((t + s.phase) & 1);
-        if (layout == LBM_AB_PULL) return GATHER_PULL_AB;
+        if (layout == LBM_AB_PULL) return s.P.nee ? GATHER_NEE_AB : GATHER_PULL_AB;
         return odd ? GATHER_PULL_AA : GATHER_LOCAL;
     }
     const void* cur_of(const Slot& s) const {
@@ -280,6 +286,7 @@ lbm_status sync_tables(lbm_batch* b) {
     b->h_owner.clear();
     std::vector<WallSpec> walls(b->capacity);
     int tiles = 0;
+    b->has_nee = false;
     for (int k = 0; k < b->capacity; ++k) {
         BatchInst<float>& I = b->h_table[k];
         std::memset(&I, 0, sizeof I);
@@ -312,7 +319,9 @@ lbm_status sync_tables(lbm_batch* b) {
         W.C0 = s.P.C0;
         W.dT = s.P.Tw[0] - s.P.Tw[1];
         W.dC = s.P.Cw[0] - s.P.Cw[1];
-        W.L = s.P.nx;
+        W.nee = s.P.nee;
+        W.L = s.P.nee ? s.P.nx - 1.0 : (double)s.P.nx;
+        if (s.P.nee) b->has_nee = true;
     }
     b->total_tiles = tiles;
     b->one_node_tiles = true;
@@ -380,11 +389,11 @@ int reduce_grid(const lbm_batch* b) {
 
 cudaError_t launch_range(lbm_batch* b, int tile_begin, int tile_end, int parity) {
     const bool aa = b->layout == LBM_AA;
-    const bool one = b->one_node_tiles;
+    const bool one = b->one_node_tiles, nee = b->has_nee;
     switch (b->prec) {
-        case LBM_F32: return launch_batch_step<float>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, b->stream);
-        case LBM_BF16: return launch_batch_step<__nv_bfloat16>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, b->stream);
-        default: return launch_batch_step<__half>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, b->stream);
+        case LBM_F32: return launch_batch_step<float>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, nee, b->stream);
+        case LBM_BF16: return launch_batch_step<__nv_bfloat16>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, nee, b->stream);
+        default: return launch_batch_step<__half>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, nee, b->stream);
     }
 }
 
@@ -473,6 +482,10 @@ lbm_status lbm_batch_create(const lbm_instance* inst, int count, int capacity, s
             gerr("lbm_batch_create: cavity %d: %s", k, why.c_str());
             return LBM_ERR_INVALID;
         }
+        if (inst[k].params.nee && O.layout != LBM_AB_PULL) {
+            gerr("lbm_batch_create: cavity %d: walls with nodes on them need the two-buffer layout", k);
+            return LBM_ERR_INVALID;
+        }
     }
     lbm_batch* b = new (std::nothrow) lbm_batch();
     if (!b) {
@@ -557,6 +570,8 @@ lbm_status lbm_batch_add(lbm_batch* b, const lbm_instance* inst, int* slot) {
     }
     std::string why;
     if (!params_ok(inst->params, &why)) return b->fail(LBM_ERR_INVALID, "lbm_batch_add: %s", why.c_str());
+    if (inst->params.nee && b->layout != LBM_AB_PULL)
+        return b->fail(LBM_ERR_INVALID, "lbm_batch_add: walls with nodes on them need the two-buffer layout");
     int k = -1;
     for (int q = 0; q < b->capacity; ++q)
         if (!b->slots[q].used) {

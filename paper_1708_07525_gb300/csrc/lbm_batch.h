@@ -8,10 +8,12 @@ namespace lbm {
 template <typename R> struct BatchInst;
 
 // One step of the cavities owning tiles [tile_begin, tile_end) (one CTA per tile);
-// one_node: every tile has exactly BATCH_THREADS nodes (loop-free kernel).
+// one_node: every tile has exactly BATCH_THREADS nodes (loop-free kernel); nee: some
+// cavity of the batch has wall nodes (Sec. 3.3), so the kernel with the rebuild runs.
 template <typename S>
 cudaError_t launch_batch_step(const BatchInst<float>* table, const int* owner, int tile_begin,
-                              int tile_end, int parity, bool aa, bool one_node, cudaStream_t st);
+                              int tile_end, int parity, bool aa, bool one_node, bool nee,
+                              cudaStream_t st);
 template <typename S>
 cudaError_t launch_batch_residual(const BatchInst<float>* table, const int* owner,
                                   const int* ntiles, int total_tiles, int n_inst, int parity,

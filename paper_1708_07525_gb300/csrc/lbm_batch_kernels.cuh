@@ -40,7 +40,9 @@ __device__ __forceinline__ void load_inst(const BatchInst<R>* __restrict__ table
 
 // One time step of every active cavity.  tile_owner[t] = cavity of global tile t.
 // Launched with one CTA per tile (the loop then runs once).
-template <typename S, bool AA>
+// NEE = true: the batch holds cavities with wall nodes (Sec. 3.3); their nodes gather
+// through the rebuild (two-buffer layout only).
+template <typename S, bool AA, bool NEE = false>
 __global__ void __launch_bounds__(BATCH_THREADS, 4)
 batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
                   const int* __restrict__ tile_owner, int tile_begin, int tile_end, int parity) {
@@ -67,7 +69,10 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
             if (!AA) {
                 const S* src = (const S*)I.buf[odd];
                 S* dst = (S*)I.buf[odd ^ 1];
-                gather_pull<false, true, false>(src, G, i, j, I.c, f, g, h);
+                if (NEE && I.c.nee)
+                    gather_nee(src, G, i, j, I.c, f, g, h);
+                else
+                    gather_pull<false, true, false>(src, G, i, j, I.c, f, g, h);
                 load_hist(hist, G, self, hv);
                 uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
                 collide(I.c, f, g, h, hv);
@@ -96,8 +101,8 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
 // registers (the descriptor stays in shared memory and occupancy stays high).
 // The two-buffer variant fits 64 registers without spilling (8 CTAs per SM
 // instead of 7); the in-place one would spill there and keeps its count.
-template <typename S, bool AA>
-__global__ void __launch_bounds__(BATCH_THREADS, AA ? 1 : 8)
+template <typename S, bool AA, bool NEE = false>
+__global__ void __launch_bounds__(BATCH_THREADS, (AA || NEE) ? 1 : 8)
 batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
                    const int* __restrict__ tile_owner, int tile_begin, int parity) {
     using R = typename Real<S>::type;
@@ -120,7 +125,10 @@ batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
     if (!AA) {
         const S* src = (const S*)I.buf[odd];
         S* dst = (S*)I.buf[odd ^ 1];
-        gather_pull<false, true, false>(src, G, i, j, I.c, f, g, h);
+        if (NEE && I.c.nee)
+            gather_nee(src, G, i, j, I.c, f, g, h);
+        else
+            gather_pull<false, true, false>(src, G, i, j, I.c, f, g, h);
         load_hist(hist, G, self, hv);
         uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
         collide(I.c, f, g, h, hv);
@@ -146,7 +154,7 @@ batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
 template <typename R>
 __device__ __forceinline__ int batch_mode(const BatchInst<R>& I, int parity, bool aa) {
     const int odd = (parity + I.phase) & 1;
-    if (!aa) return GATHER_PULL_AB;
+    if (!aa) return I.c.nee ? GATHER_NEE_AB : GATHER_PULL_AB;
     return odd ? GATHER_PULL_AA : GATHER_LOCAL;
 }
 template <typename R>
@@ -263,7 +271,28 @@ batch_nush_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
         const int mode = batch_mode(I, parity, AA);
         const S* buf = (const S*)batch_cur(I, parity, AA);
         const Geom G = I.G;
-        for (int j = threadIdx.x; j < G.ny; j += blockDim.x) {
+        if (W.nee) {
+            // nodes on the walls: the node stencil and the trapezoidal mean of nush_kernel
+            for (int j = threadIdx.x; j < G.ny; j += blockDim.x) {
+                R f[9], g[5], h[5];
+                double T[6], C[6];
+                const int cols[6] = {0, 1, 2, G.nx - 3, G.nx - 2, G.nx - 1};
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    gather<false>(mode, buf, G, cols[q], j, I.c, f, g, h);
+                    const R sg = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+                    const R sh = ((h[0] + h[1]) + (h[2] + h[3])) + h[4];
+                    T[q] = W.T0 + (double)(sg * I.c.inv_sigma);
+                    C[q] = W.C0 + (double)(sh * I.c.inv_eps);
+                }
+                const double wj = (j == 0 || j == G.ny - 1) ? 0.5 : 1.0;
+                acc[0] += wj * -W.L * (-3.0 * T[0] + 4.0 * T[1] - T[2]) / 2.0 / W.dT;
+                acc[1] += wj * -W.L * (-3.0 * C[0] + 4.0 * C[1] - C[2]) / 2.0 / W.dC;
+                acc[2] += wj * -W.L * (3.0 * T[5] - 4.0 * T[4] + T[3]) / 2.0 / W.dT;
+                acc[3] += wj * -W.L * (3.0 * C[5] - 4.0 * C[4] + C[3]) / 2.0 / W.dC;
+            }
+        }
+        for (int j = threadIdx.x; j < G.ny && !W.nee; j += blockDim.x) {
             R f[9], g[5], h[5];
             double T[4], C[4];
             const int cols[4] = {0, 1, G.nx - 2, G.nx - 1};
@@ -292,7 +321,7 @@ batch_nush_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
     if (threadIdx.x < 4) {
         double s = 0;
         for (int w = 0; w < BATCH_THREADS / 32; ++w) s += red[w][threadIdx.x];
-        out[(size_t)k * 4 + threadIdx.x] = I.active ? s / I.G.ny : 0.0;
+        out[(size_t)k * 4 + threadIdx.x] = I.active ? s / (W.nee ? I.G.ny - 1.0 : (double)I.G.ny) : 0.0;
     }
 }
 

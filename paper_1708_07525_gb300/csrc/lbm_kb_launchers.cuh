@@ -7,18 +7,23 @@ namespace lbm {
 
 template <typename S>
 cudaError_t launch_batch_step(const BatchInst<float>* table, const int* owner, int tile_begin,
-                              int tile_end, int parity, bool aa, bool one_node, cudaStream_t st) {
+                              int tile_end, int parity, bool aa, bool one_node, bool nee,
+                              cudaStream_t st) {
     const int grid = tile_end - tile_begin;
     if (grid <= 0) return cudaSuccess;
     if (one_node) {
         if (aa)
             batch_step1_kernel<S, true><<<grid, BATCH_THREADS, 0, st>>>(table, owner, tile_begin, parity);
+        else if (nee)
+            batch_step1_kernel<S, false, true><<<grid, BATCH_THREADS, 0, st>>>(table, owner, tile_begin, parity);
         else
             batch_step1_kernel<S, false><<<grid, BATCH_THREADS, 0, st>>>(table, owner, tile_begin, parity);
         return cudaGetLastError();
     }
     if (aa)
         batch_step_kernel<S, true><<<grid, BATCH_THREADS, 0, st>>>(table, owner, tile_begin, tile_end, parity);
+    else if (nee)
+        batch_step_kernel<S, false, true><<<grid, BATCH_THREADS, 0, st>>>(table, owner, tile_begin, tile_end, parity);
     else
         batch_step_kernel<S, false><<<grid, BATCH_THREADS, 0, st>>>(table, owner, tile_begin, tile_end, parity);
     return cudaGetLastError();
@@ -64,7 +69,7 @@ int batch_step_blocks_per_sm(bool aa) {
 
 #define LBM_BATCH_INSTANTIATE(S)                                                                  \
     template cudaError_t launch_batch_step<S>(const BatchInst<float>*, const int*, int, int, int,  \
-                                              bool, bool, cudaStream_t);                           \
+                                              bool, bool, bool, cudaStream_t);                     \
     template cudaError_t launch_batch_residual<S>(const BatchInst<float>*, const int*, const int*, \
                                                   int, int, int, bool, int, double*, double*,      \
                                                   cudaStream_t);                                   \

@@ -145,3 +145,36 @@ def test_l2_blocking_keeps_results_bitwise(layout):
         fa, fb = a.fields(k), b.fields(k)
         for key in KEYS:
             assert np.array_equal(fa[key], fb[key]), (k, key)
+
+
+def test_wall_node_cavities_in_a_batch_equal_the_single_cavity_bitwise():
+    """Cavities with the paper's own walls (Sec. 3.3, a convective wall) share a batch with
+    halfway-wall cavities: each gives bit for bit the fields of the single-cavity path
+    (the same per-node arithmetic), and Nu / Sh with the node stencil."""
+    pc = lbm.lbm_derive_params_convective(40, 1e4, 1e-2, 0.6, 1.0, 1.0, 1.0, 1.0, 200.0)
+    pn = lbm.lbm_derive_params_nee(37, 29, 5e4, 1e-2, 0.6, 1.0, 3.0, -1.5)
+    insts = [lbm.make_instance(MIX[0]), lbm.make_instance(params=pc, seed=3, noise=0.02),
+             lbm.make_instance(MIX[1]), lbm.make_instance(params=pn, seed=5, noise=0.02)]
+    b = lbm.Batch(insts, precision="f32")
+    b.step(357)
+    nush = b.nusselt_sherwood()
+    for k, (p, seed) in ((1, (pc, 3)), (3, (pn, 5))):
+        single = lbm.Cavity(params=p, precision="f32", seed=seed, noise=0.02)
+        single.step(357)
+        fs, fb = single.fields(), b.fields(k)
+        for key in KEYS:
+            assert np.array_equal(fs[key], fb[key]), (k, key)
+        np.testing.assert_allclose(nush[k], single.nusselt_sherwood(), rtol=1e-12)
+        single.close()
+    # the halfway cavities of the same batch are untouched by the wall-node kernel
+    alone = lbm.Batch([lbm.make_instance(MIX[1])], precision="f32")
+    alone.step(357)
+    for key in KEYS:
+        assert np.array_equal(alone.fields(0)[key], b.fields(2)[key]), key
+
+
+def test_wall_node_cavity_rejected_by_in_place_batches():
+    pc = lbm.lbm_derive_params_convective(40, 1e4, 1e-2, 0.6, 1.0, 1.0, 1.0, 1.0, 1.0)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Batch([lbm.make_instance(params=pc)], precision="f32", layout="aa")
+    assert ei.value.status == lbm.ERR_INVALID

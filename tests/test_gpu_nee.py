@@ -247,3 +247,15 @@ def test_checkpoint_resume_with_wall_nodes_bitwise():
     assert ei.value.status == lbm.ERR_INVALID
     for x in (a, b, c):
         x.close()
+
+
+@pytest.mark.parametrize("nx,ny", [(5, 5), (5, 9), (11, 5)])
+def test_smallest_wall_node_grids_f64(oracle_mod, nx, ny):
+    """The smallest grids the rebuild allows (x_ff two nodes in from each wall): every
+    node is within two of a wall, corners meet, and a convective wall is on."""
+    edits = dict(BiT=(0, 1.5, 0, 0), BiC=(0, 0.5, 0, 0))
+    gpu, ora = nee_pair(oracle_mod, nx, ny, (1e4, 1e-2, 0.6, 1.0, 2.0, 1.0), edits, noise=0.05)
+    gpu.step(300)
+    ora.step(300)
+    check(gpu, ora, 1e-12, nush_tol=1e-11, tb=False)
+    gpu.close()

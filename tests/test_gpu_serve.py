@@ -68,3 +68,26 @@ def test_step_cap_and_divergence_statuses():
     res = {r["id"]: r for r in srv.drain()}
     assert res[1]["status"] == lbm.ERR_UNCONVERGED and res[1]["steps"] == 60
     assert res[2]["status"] == lbm.ERR_DIVERGED
+
+
+def test_wall_node_requests_alone_equal_in_mix():
+    """Requests with the paper's own walls and convective walls (Sec. 3.3, Eq. 39) are
+    served beside halfway-wall requests; each result equals the request served alone."""
+    mixed = requests(6, seed=31)
+    walls = [lbm.make_instance(params=lbm.lbm_derive_params_convective(n, 1e4, 1e-2, 0.6, 1.0,
+                                                                         1.0, 1.0, 1.0, bic),
+                               seed=7 + n, noise=1e-3)
+             for n, bic in ((32, 1.0), (40, 200.0))]
+    reqs = mixed[:3] + walls + mixed[3:]
+    budget = sum(lbm.batch_instance_bytes(r.params.nx, r.params.ny, "f32") for r in reqs) * 2
+    mix = lbm.Server(budget, max_slots=16, check_every=50, precision="f32")
+    for k, r in enumerate(reqs):
+        mix.submit(r, tol=1e-4, max_steps=3000, rid=k)
+    got = {r["id"]: r for r in mix.drain()}
+    for k in (3, 4, 0):
+        solo = lbm.Server(budget, max_slots=2, check_every=50, precision="f32")
+        solo.submit(reqs[k], tol=1e-4, max_steps=3000, rid=k)
+        (res,) = solo.drain()
+        assert res["status"] == got[k]["status"]
+        assert res["steps"] == got[k]["steps"]
+        assert res["nush"] == got[k]["nush"]
