@@ -570,8 +570,9 @@ def run_precision(args):
             rec["nush_rel_err"] = float(np.max(np.abs(np.array(hist[-1][2:]) - ref[1]) / np.abs(ref[1])))
         out[prec] = rec
         c.close()
-        with open(os.path.join(ROOT, "gpurun_out", "precision_partial.json"), "w") as f:
-            json.dump(out, f)
+        if args.partial_out:   # results so far, in case a long study is cut short
+            with open(args.partial_out, "w") as f:
+                json.dump(out, f)
     line = {"metric": METRIC, "mode": "precision", "unit": "relative error", "data": "synthetic",
             "config": {"workload": f"{spec.nx}x{spec.ny} cavity Ra={spec.Ra} Da={spec.Da} eps={spec.eps} "
                                    f"Le={spec.Le} N={spec.N}", "steps": steps, "check_every": check},
@@ -612,13 +613,13 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=8.0)
     ap.add_argument("--plain-budget-s", type=float, default=120.0)
     ap.add_argument("--plain-cache", default="")
+    ap.add_argument("--partial-out", default="")
     args = ap.parse_args()
     if args.mode == "batch":
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
     if args.mode == "precision":
-        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
         return run_precision(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

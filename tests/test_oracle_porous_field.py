@@ -1,5 +1,5 @@
-"""Spatially varying porosity and permeability (the REV model applied per node,
-SURVEY §8f-4): pins of the oracle.
+"""Spatially varying porosity and permeability (the REV model applied per node):
+pins of the oracle.
 
 * A uniform field reproduces the scalar-parameter run bit for bit.
 * Fully developed channel flow through a medium whose eps(y) and K(y) vary
