@@ -340,11 +340,15 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int trial_steps, char* report, size_
  * tile_h >= 1, tile_w * tile_h <= 4096).  Results do not depend on it. */
 lbm_status lbm_batch_set_tile(lbm_batch* b, int slot, int tile_w, int tile_h);
 
-/* L2 temporal blocking: cavities are grouped so that a group's per-step working
- * set stays within l2_bytes (0 -> keep; default half the L2), and each group is
- * advanced `steps` steps (default 16) before the next, so that its state is read
- * from L2 rather than HBM on all but the first of them.  steps = 1 turns it off.
- * Results do not depend on it. */
+/* L2 temporal blocking: cavities are grouped so that the per-step working sets
+ * of the two groups in flight stay within l2_bytes (each group's within half of
+ * it; 0 -> keep; default half the L2), and each group is advanced `steps` steps
+ * (default 32) at a time, so that its state is read from L2 rather than HBM on
+ * all but the first of them.  The groups are dealt alternately to the batch's
+ * stream and a second stream the batch owns (forked from and joined back to
+ * the batch's stream, also inside its CUDA graphs), so that one group's launches
+ * fill the gaps of the other's.  steps = 1 turns blocking off (one launch over
+ * all tiles per step).  Results do not depend on it. */
 lbm_status lbm_batch_set_blocking(lbm_batch* b, int steps, size_t l2_bytes);
 
 /* Number of slots, slots in use, and the arena size / bytes in use. */

@@ -192,8 +192,14 @@ struct lbm_batch {
     // L2 temporal blocking: groups of cavities whose working set fits in a share of
     // L2 are advanced `tblock` steps each before the next group is touched.
     std::vector<std::pair<int, int>> groups;   // [tile_begin, tile_end)
+    // Groups are independent, so they are dealt round-robin to kLanes streams (the
+    // batch's own and kLanes - 1 more): one lane's launches fill the others' wave
+    // tails and launch gaps.  The kLanes groups in flight share the L2 budget.
+    static constexpr int kLanes = 2;
+    cudaStream_t lane[kLanes - 1] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kLanes - 1] = {};
     size_t l2_budget = 64u << 20;
-    int tblock = 16;
+    int tblock = 32;
     bool dirty = true;
     int64_t t = 0;
     cudaStream_t stream = nullptr;
@@ -340,7 +346,7 @@ lbm_status sync_tables(lbm_batch* b) {
             const size_t w = (b->layout == LBM_AA ? 1 : 2) * (size_t)NQ * s.G.plane * esize(b->prec) +
                              (size_t)4 * s.G.plane * sizeof(float);
             const int t0 = b->h_table[k].tile_begin;
-            if (ws > 0 && ws + w > b->l2_budget) {
+            if (ws > 0 && ws + w > b->l2_budget / lbm_batch::kLanes) {
                 b->groups.push_back({gbeg, t0});
                 gbeg = t0;
                 ws = 0;
@@ -387,31 +393,54 @@ int reduce_grid(const lbm_batch* b) {
     return std::max(1, std::min(b->sms * b->bps, std::max(1, b->total_tiles)));
 }
 
-cudaError_t launch_range(lbm_batch* b, int tile_begin, int tile_end, int parity) {
+cudaError_t launch_range(lbm_batch* b, int tile_begin, int tile_end, int parity, cudaStream_t st) {
     const bool aa = b->layout == LBM_AA;
     const bool one = b->one_node_tiles, nee = b->has_nee;
     switch (b->prec) {
-        case LBM_F32: return launch_batch_step<float>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, nee, b->stream);
-        case LBM_BF16: return launch_batch_step<__nv_bfloat16>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, nee, b->stream);
-        default: return launch_batch_step<__half>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, nee, b->stream);
+        case LBM_F32: return launch_batch_step<float>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, nee, st);
+        case LBM_BF16: return launch_batch_step<__nv_bfloat16>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, nee, st);
+        default: return launch_batch_step<__half>(b->d_table, b->d_owner, tile_begin, tile_end, parity, aa, one, nee, st);
+    }
+}
+
+void destroy_lanes(lbm_batch* b) {
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    for (int l = 0; l + 1 < lbm_batch::kLanes; ++l) {
+        if (b->ev_join[l]) cudaEventDestroy(b->ev_join[l]);
+        if (b->lane[l]) cudaStreamDestroy(b->lane[l]);
     }
 }
 
 // One step of every cavity (one launch over all tiles).
 cudaError_t launch_step(lbm_batch* b) {
-    cudaError_t e = launch_range(b, 0, b->total_tiles, b->parity());
+    cudaError_t e = launch_range(b, 0, b->total_tiles, b->parity(), b->stream);
     b->t += 1;
     return e;
 }
 
 // k steps of every cavity, group by group: each group's k launches run back to
-// back, so its state stays in L2 between them.  Every cavity sees the same
-// sequence of steps as with launch_step.
+// back, so its state stays in L2 between them.  Group i runs on lane i mod kLanes
+// (lane 0 is the batch's stream; the others are forked from it and joined back at
+// the end, also inside a captured graph).  Every cavity sees the same sequence of
+// steps as with launch_step.
 cudaError_t launch_block(lbm_batch* b, int k) {
+    const int lanes = (int)std::min<size_t>(lbm_batch::kLanes, b->groups.size());
     cudaError_t e = cudaSuccess;
-    for (const auto& g : b->groups)
+    if (lanes > 1) e = cudaEventRecord(b->ev_fork, b->stream);
+    for (int l = 1; l < lanes && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(b->lane[l - 1], b->ev_fork, 0);
+    for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+        const auto& g = b->groups[gi];
+        const int l = (int)(gi % (size_t)lanes);
+        const cudaStream_t st = l == 0 ? b->stream : b->lane[l - 1];
         for (int s = 0; s < k && e == cudaSuccess; ++s)
-            e = launch_range(b, g.first, g.second, (int)((b->t + s) & 1));
+            e = launch_range(b, g.first, g.second, (int)((b->t + s) & 1), st);
+    }
+    // join even after a failed launch, so that a capture is never left forked
+    for (int l = 1; l < lanes; ++l) {
+        cudaError_t j = cudaEventRecord(b->ev_join[l - 1], b->lane[l - 1]);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(b->stream, b->ev_join[l - 1], 0);
+        if (e == cudaSuccess) e = j;
+    }
     b->t += k;
     return e;
 }
@@ -505,7 +534,9 @@ lbm_status lbm_batch_create(const lbm_instance* inst, int count, int capacity, s
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     int l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device);
-    if (l2 > 0) b->l2_budget = (size_t)l2 * 3 / 4;
+    // half of L2 for the groups in flight (GB300, 512 mixed cavities: 1/2 beat 3/4 by 1 %
+    // two-buffer and 28 % in place; a whole L2 lost 15 % / 10 %)
+    if (l2 > 0) b->l2_budget = (size_t)l2 / 2;
     if (O.stream) {
         b->stream = (cudaStream_t)O.stream;
     } else {
@@ -515,6 +546,17 @@ lbm_status lbm_batch_create(const lbm_instance* inst, int count, int capacity, s
             return s;
         }
         b->own_stream = true;
+    }
+    bool lanes_ok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int l = 0; l + 1 < lbm_batch::kLanes && lanes_ok; ++l)
+        lanes_ok = cudaStreamCreateWithFlags(&b->lane[l], cudaStreamNonBlocking) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&b->ev_join[l], cudaEventDisableTiming) == cudaSuccess;
+    if (!lanes_ok) {
+        lbm_status s = b->fail(LBM_ERR_CUDA, "lbm_batch_create: lane streams / events failed");
+        destroy_lanes(b);
+        if (b->own_stream) cudaStreamDestroy(b->stream);
+        delete b;
+        return s;
     }
     if (b->stream == nullptr || b->stream == cudaStreamLegacy || b->stream == cudaStreamPerThread)
         b->graph_chunk = 0;
@@ -677,6 +719,10 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
     while (n >= tb && tb > 1 && e == cudaSuccess) {
         e = launch_block(b, tb);
         n -= tb;
+    }
+    if (n > 0 && tb > 1 && e == cudaSuccess) {   // the rest as one shorter block
+        e = launch_block(b, n);
+        n = 0;
     }
     while (n > 0 && e == cudaSuccess) {
         e = launch_step(b);
@@ -944,6 +990,7 @@ void lbm_batch_destroy(lbm_batch* b) {
     b->dfree(b->d_owner);
     b->dfree(b->d_partial);
     b->dfree(b->d_fields);
+    destroy_lanes(b);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }
