@@ -100,9 +100,11 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
 // one tile per CTA and no loop, so nothing loop-invariant is hoisted into
 // registers (the descriptor stays in shared memory and occupancy stays high).
 // The two-buffer variant fits 64 registers without spilling (8 CTAs per SM
-// instead of 7); the in-place one would spill there and keeps its count.
+// instead of 7).  The in-place one holds both parities' code (cavities in one
+// launch may be at different parities) and was compiled to 146 registers (3 CTAs
+// per SM) when left alone; held to 5 CTAs per SM it fits 96 without spilling.
 template <typename S, bool AA, bool NEE = false>
-__global__ void __launch_bounds__(BATCH_THREADS, (AA || NEE) ? 1 : 8)
+__global__ void __launch_bounds__(BATCH_THREADS, NEE ? 1 : (AA ? 5 : 8))
 batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
                    const int* __restrict__ tile_owner, int tile_begin, int parity) {
     using R = typename Real<S>::type;
