@@ -190,7 +190,7 @@ struct lbm_batch {
     bool one_node_tiles = false;         // every tile has BATCH_THREADS nodes
     bool has_nee = false;                // some cavity has wall nodes (Sec. 3.3)
     // L2 temporal blocking: groups of cavities whose working set fits in a share of
-    // L2 are advanced `tblock` steps each before the next group is touched.
+    // L2 are advanced `tblock` steps at a time.
     std::vector<std::pair<int, int>> groups;   // [tile_begin, tile_end)
     // Groups are independent, so they are dealt round-robin to kLanes streams (the
     // batch's own and kLanes - 1 more): one lane's launches fill the others' wave
@@ -534,8 +534,8 @@ lbm_status lbm_batch_create(const lbm_instance* inst, int count, int capacity, s
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     int l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device);
-    // half of L2 for the groups in flight (GB300, 512 mixed cavities: 1/2 beat 3/4 by 1 %
-    // two-buffer and 28 % in place; a whole L2 lost 15 % / 10 %)
+    // half of L2 for the groups in flight (GB300, 512 mixed cavities, two-buffer: 1/2
+    // beat 3/4 by 1 % and a whole L2 by 15 %)
     if (l2 > 0) b->l2_budget = (size_t)l2 / 2;
     if (O.stream) {
         b->stream = (cudaStream_t)O.stream;
