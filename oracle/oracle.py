@@ -68,7 +68,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
+            # LBM_ORACLE_LIB names another compiled copy of the oracle to load instead
+            # (the planted-mistake test builds altered copies and runs the pins on them)
+            L = C.CDLL(os.environ.get("LBM_ORACLE_LIB") or build())
             P = C.POINTER(Params)
             dp = C.POINTER(C.c_double)
             L.or_derive.argtypes = [P]

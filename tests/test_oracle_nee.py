@@ -11,6 +11,10 @@ convective (Robin) wall of Eq. 39.
   H != L the Biot number keeps the width L as its length scale.
 * The Brinkman-Darcy channel between no-slip walls at y = 0 and y = H = ny - 1:
   second-order convergence to the closed form of Eqs. 2 and 5.
+* Couette flow between a resting wall node row and a moving one: the linear
+  profile u = U y / H is reproduced exactly for any viscosity (the extrapolated
+  non-equilibrium part of Eq. 33 carries the wall shear; the equilibrium alone
+  misses it by ~1e-3).
 * Sec. 3.2's claim on a convective cavity: at Le = 1 and equal wall data, the
   steady T and C coincide and Nu = Sh; the coupled equilibria of "model A"
   (Eqs. 30-32) break the equality.
@@ -170,6 +174,34 @@ def test_nee_brinkman_channel_second_order(oracle_mod):
     order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert errs[-1] < 1e-3, errs
     assert order.min() > 1.8, (errs, order)
+
+
+@pytest.mark.parametrize("s_nu", [0.7, 1.0, 1.6])
+def test_nee_couette_exact(oracle_mod, s_nu):
+    """Wall nodes at j = 0 (at rest) and j = H = ny - 1 (moving with U, Eq. 33 with
+    u_w = (U, 0)), periodic x, no medium: u = U y / H at every node."""
+    O = oracle_mod
+    ny, U = 16, 0.05
+    p = O.derive(5, ny, 1e4, 1e-2, 0.7, 1, 1, 0, nee=True)
+    p.periodic_x = 1
+    p.gbT = p.gbC = 0.0
+    p.Feps = 0.0
+    p.K = 1e300
+    p.s[7] = p.s[8] = s_nu
+    p.nu_e = p.nu = (1 / s_nu - 0.5) / 3.0
+    p.uw[3][0] = U
+    o = O.Oracle(p, seed=1, noise=0.0)
+    prev = None
+    for _ in range(400):
+        o.step(500)
+        u = o.fields()["ux"][:, 0].copy()
+        if prev is not None and np.abs(u - prev).max() < 1e-16:
+            break
+        prev = u
+    fl = o.fields()
+    exact = U * np.arange(ny) / (ny - 1)
+    np.testing.assert_allclose(fl["ux"], np.broadcast_to(exact[:, None], fl["ux"].shape), rtol=0, atol=1e-13)
+    assert np.abs(fl["uy"]).max() < 1e-14
 
 
 def _steady(O, p, tol=1e-11, chunk=2000, cap=150):

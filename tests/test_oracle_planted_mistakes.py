@@ -1,0 +1,112 @@
+"""The pins catch plausible mistakes in the oracle.
+
+Each case plants one mistake in a copy of oracle/lbm_oracle.c (a dropped term, a wrong
+sign, coefficient or index, a transposed operand), compiles the copy, and runs the pin
+tests that should notice it against that copy (LBM_ORACLE_LIB): they must fail.  The
+oracle itself is never altered; its unaltered pins run in the rest of the suite.
+
+If the oracle's source is rewritten so that a planted expression no longer appears
+verbatim, the case fails and names it, so that the list follows the source.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+COLL = "tests/test_oracle_collision.py"
+PHYS = "tests/test_oracle_physics.py"
+WALLS = "tests/test_oracle_walls.py"
+FIELD = "tests/test_oracle_porous_field.py"
+NEE = "tests/test_oracle_nee.py"
+
+# (what is planted, the correct expression, the mistaken one, the pins that must fail)
+MISTAKES = [
+    ("sign of S_7 in the forcing moments (Eq. 15)",
+     "2.0 * rho0 * (ux * Fx - uy * Fy) / eps,", "-2.0 * rho0 * (ux * Fx - uy * Fy) / eps,", [COLL]),
+    ("alpha_2 = -2 instead of -3 (Eq. 14, Sec. 3.1)",
+     "double a1 = 1.0, a2 = -3.0;", "double a1 = 1.0, a2 = -2.0;", [COLL]),
+    ("sign of the explicit d(T u)/dt (Eq. 27, Sec. 3.2)",
+     "double XTx = Tux - hist[0], XTy = Tuy - hist[1];",
+     "double XTx = hist[0] - Tux, XTy = hist[1] - Tuy;", [COLL]),
+    ("model A's equilibrium (Eq. 30) in place of Eq. 24",
+     ": -4.0 * cap * Phi + 5.0 * varpi * Phi;", ": (-4.0 + 5.0 * varpi) * cap * Phi;", [COLL]),
+    ("eps dropped from the buoyancy half-force of v (Eq. 19)",
+     "double vy = jy / p->rho0 + 0.5 * eps * Gy;", "double vy = jy / p->rho0 + 0.5 * Gy;", [COLL]),
+    ("sign of the anti-bounce-back of a Dirichlet wall",
+     "s->g2[opp[q] * n + x] = -gs[q] + 2.0 * wt_axis * kg * p->Tw[side];",
+     "s->g2[opp[q] * n + x] = gs[q] + 2.0 * wt_axis * kg * p->Tw[side];", [WALLS]),
+    ("source term dropped from the D2Q5 collision (Eqs. 21-22, 27)",
+     "ns[k] = n[k] - rates[k] * (n[k] - neq[k]) + (1.0 - 0.5 * rates[k]) * S[k];",
+     "ns[k] = n[k] - rates[k] * (n[k] - neq[k]);", [COLL]),
+    ("eps dropped from l_0 (Eq. 19)",
+     "double l0 = 0.5 * (1.0 + eps * 0.5 * p->nu / p->K);",
+     "double l0 = 0.5 * (1.0 + 0.5 * p->nu / p->K);", [COLL]),
+    ("eps dropped from the Forchheimer force (Eq. 5)",
+     "- eps * p->Feps / sqrt(p->K) * umag * ux", "- p->Feps / sqrt(p->K) * umag * ux", [COLL]),
+    ("eps dropped from the Darcy force (Eq. 5)",
+     "double Fx = -eps * p->nu / p->K * ux", "double Fx = -p->nu / p->K * ux", [COLL]),
+    ("Nu length scale nx - 1 with halfway walls (Eq. 38)",
+     "nuL += -nx * dTdx_L / dT;", "nuL += -(nx - 1) * dTdx_L / dT;", [PHYS]),
+    ("M^-1 transposed in the back-transform",
+     "fs[i] += M9inv[i][k] * ms[k];", "fs[i] += M9inv[k][i] * ms[k];", [COLL]),
+    ("N transposed in the D2Q5 source moments (Eq. 27)",
+     "for (int i = 0; i < 5; ++i) S[k] += N5[k][i] * St[i];",
+     "for (int i = 0; i < 5; ++i) S[k] += N5[i][k] * St[i];", [COLL]),
+    ("C from sigma instead of eps (Eq. 26)",
+     "double C = sh / p->eps;", "double C = sh / p->sigma;", [COLL]),
+    ("eps^2 instead of eps^3 in F_eps (Eq. 7)",
+     "p->Feps = 1.75 / sqrt(150.0 * p->eps * p->eps * p->eps);",
+     "p->Feps = 1.75 / sqrt(150.0 * p->eps * p->eps);", [FIELD]),
+    ("wrong rate with the forcing moments (Eq. 10)",
+     "ms[k] = m[k] - p->s[k] * (m[k] - meq[k]) + (1.0 - 0.5 * p->s[k]) * S[k];",
+     "ms[k] = m[k] - p->s[k] * (m[k] - meq[k]) + (1.0 - 0.5 * p->s[8 - k]) * S[k];", [COLL]),
+    ("non-equilibrium part dropped at wall nodes (Eq. 33)",
+     "F[q * n + xb] = eb + ff[q] - ef;", "F[q * n + xb] = eb;", [NEE + "::test_nee_couette_exact"]),
+    ("sign of the convective wall term (Eq. 39)",
+     "return (4.0 * Phi_f - Phi_ff + 2.0 * b) / (3.0 + 2.0 * a);",
+     "return (4.0 * Phi_f - Phi_ff - 2.0 * b) / (3.0 - 2.0 * a);", [NEE + "::test_convective_right_wall_exact"]),
+    ("weights of the one-sided gradient (Eqs. 36-37)",
+     "(4.0 * Phi_f - Phi_ff + 2.0 * b)", "(4.0 * Phi_f - 2.0 * Phi_ff + 2.0 * b)",
+     [NEE + "::test_convective_right_wall_exact"]),
+    ("Nu length scale nx with wall nodes",
+     "        const double L = (double)(nx - 1);", "        const double L = (double)nx;",
+     [NEE + "::test_nee_dirichlet_conduction_exact"]),
+]
+
+
+def _build(tmp, k, src):
+    c = os.path.join(tmp, f"planted_{k}.c")
+    so = os.path.join(tmp, f"planted_{k}.so")
+    with open(c, "w") as f:
+        f.write(src)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-I", ORACLE,
+                    "-o", so, c, "-lm"], check=True, capture_output=True)
+    return so
+
+
+def _pins_fail(so, targets):
+    env = dict(os.environ, LBM_ORACLE_LIB=so, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", *targets, "-x", "-q", "-m", "not gpu",
+                        "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=600)
+    return r.returncode, r.stdout[-800:]
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="gcc is needed to build the altered copies")
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    with open(os.path.join(ORACLE, "lbm_oracle.c")) as f:
+        src = f.read()
+    for what, good, _, _ in MISTAKES:
+        assert src.count(good) == 1, f"'{what}': the expression is not in the oracle exactly once"
+    sos = [_build(str(tmp_path), k, src.replace(good, bad)) for k, (_, good, bad, _) in enumerate(MISTAKES)]
+    workers = max(1, min(4, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        results = list(ex.map(lambda a: _pins_fail(*a), [(so, m[3]) for so, m in zip(sos, MISTAKES)]))
+    missed = [(m[0], out) for m, (rc, out) in zip(MISTAKES, results) if rc != 1]
+    assert not missed, "planted mistakes not caught (pytest exit code != 1):\n" + "\n".join(
+        f"- {w}:\n{o}" for w, o in missed)
