@@ -199,9 +199,14 @@ def test_nee_couette_exact(oracle_mod, s_nu):
             break
         prev = u
     fl = o.fields()
-    exact = U * np.arange(ny) / (ny - 1)
+    y, H = np.arange(ny), ny - 1
+    exact = U * y / H
     np.testing.assert_allclose(fl["ux"], np.broadcast_to(exact[:, None], fl["ux"].shape), rtol=0, atol=1e-13)
     assert np.abs(fl["uy"]).max() < 1e-14
+    # stream function from the wall node (psi = 0): U y^2 / (2 H)
+    psi = o.stream_function()
+    np.testing.assert_allclose(psi, np.broadcast_to((U * y ** 2 / (2 * H))[:, None], psi.shape),
+                               rtol=0, atol=2e-12)   # ny velocity errors of <= 1e-13 summed
 
 
 def _steady(O, p, tol=1e-11, chunk=2000, cap=150):

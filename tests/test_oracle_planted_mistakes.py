@@ -23,6 +23,7 @@ PHYS = "tests/test_oracle_physics.py"
 WALLS = "tests/test_oracle_walls.py"
 FIELD = "tests/test_oracle_porous_field.py"
 NEE = "tests/test_oracle_nee.py"
+DERIVE = "tests/test_oracle_derive.py"
 
 # (what is planted, the correct expression, the mistaken one, the pins that must fail)
 MISTAKES = [
@@ -76,6 +77,30 @@ MISTAKES = [
     ("Nu length scale nx with wall nodes",
      "        const double L = (double)(nx - 1);", "        const double L = (double)nx;",
      [NEE + "::test_nee_dirichlet_conduction_exact"]),
+    ("J dropped from s_nu (Sec. 4.1)",
+     "double inv_snu = 0.5 + p->Ma * p->J * L * sqrt(p->Pr) / (sqrt(p->cs2) * sqrt(p->Ra));",
+     "double inv_snu = 0.5 + p->Ma * L * sqrt(p->Pr) / (sqrt(p->cs2) * sqrt(p->Ra));", [DERIVE]),
+    ("Pr for sqrt(Pr) in s_nu (Sec. 4.1)",
+     "double inv_snu = 0.5 + p->Ma * p->J * L * sqrt(p->Pr) / (sqrt(p->cs2) * sqrt(p->Ra));",
+     "double inv_snu = 0.5 + p->Ma * p->J * L * p->Pr / (sqrt(p->cs2) * sqrt(p->Ra));", [DERIVE]),
+    ("length scale nx with wall nodes in the mapping",
+     "double L = p->nee ? (double)(p->nx - 1) : (double)p->nx;", "double L = (double)p->nx;", [DERIVE]),
+    ("c_sT^2 = varpi / 3",
+     "p->csT2 = p->varpi / 2.0;", "p->csT2 = p->varpi / 3.0;", [DERIVE]),
+    ("D_e = alpha_e Le",
+     "p->D_e = p->alpha_e / p->Le;", "p->D_e = p->alpha_e * p->Le;", [DERIVE]),
+    ("nu = nu_e J",
+     "p->nu = p->nu_e / p->J;", "p->nu = p->nu_e * p->J;", [DERIVE]),
+    ("g beta_T dT = U^2 / L^2",
+     "p->gbT = p->U * p->U / L;", "p->gbT = p->U * p->U / (L * L);", [DERIVE]),
+    ("sign of the moving-wall term of the bounce-back",
+     "s->f2[opp[q] * n + x] = fs[q] - 2.0 * W9[q] * p->rho0 * eu / p->cs2;",
+     "s->f2[opp[q] * n + x] = fs[q] + 2.0 * W9[q] * p->rho0 * eu / p->cs2;", [WALLS]),
+    ("stream function without the half cell below the first node",
+     "double acc = p->nee ? 0.0 : 0.25 * ux[i];", "double acc = 0.0;", [WALLS + "::test_couette_exact"]),
+    ("stream function with rectangles for trapezoids",
+     "acc += 0.5 * (ux[(size_t)(j - 1) * nx + i] + ux[(size_t)j * nx + i]);",
+     "acc += ux[(size_t)j * nx + i];", [NEE + "::test_nee_couette_exact"]),
 ]
 
 

@@ -2,7 +2,8 @@
 (used by the lid-driven cavity of Sec. 4.3).
 
 * Couette flow between a resting bottom wall and a top wall moving with U: the
-  steady profile u = U y / H is reproduced exactly by halfway bounce-back.
+  steady profile u = U y / H is reproduced exactly by halfway bounce-back, and the
+  stream function (psi = 0 on the bottom wall) is its integral U y^2 / (2 H).
 * Porous Couette flow (Eqs. 2, 5 with F_eps = 0): nu_e u'' - (eps nu / K) u = 0,
   u(0) = 0, u(H) = U => u = U sinh(r y) / sinh(r H), r^2 = eps nu / (K nu_e);
   second-order convergence.
@@ -30,7 +31,9 @@ def couette(O, ny, U, K=1e300, eps=0.7, s_nu=1.0, steps_max=400):
         if prev is not None and np.abs(u - prev).max() < 1e-16:
             break
         prev = u
-    return p, o.fields()
+    fl = o.fields()
+    fl["psi"] = o.stream_function()
+    return p, fl
 
 
 @pytest.mark.parametrize("s_nu", [0.7, 1.0, 1.6])
@@ -40,6 +43,11 @@ def test_couette_exact(oracle_mod, s_nu):
     y = np.arange(ny) + 0.5
     np.testing.assert_allclose(fl["ux"][:, 0], U * y / ny, rtol=0, atol=1e-13)
     assert np.abs(fl["uy"]).max() < 1e-14
+    # stream function (u_x = d psi / dy, psi = 0 on the bottom wall at y = 0): the
+    # integral of the linear profile, U y^2 / (2 H), exact for the trapezoid rule
+    exact_psi = U * y ** 2 / (2 * ny)
+    np.testing.assert_allclose(fl["psi"], np.broadcast_to(exact_psi[:, None], fl["psi"].shape),
+                               rtol=0, atol=2e-12)   # ny velocity errors of <= 1e-13 summed
 
 
 def test_porous_couette_closed_form(oracle_mod):
