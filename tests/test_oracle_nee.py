@@ -15,6 +15,10 @@ convective (Robin) wall of Eq. 39.
   profile u = U y / H is reproduced exactly for any viscosity (the extrapolated
   non-equilibrium part of Eq. 33 carries the wall shear; the equilibrium alone
   misses it by ~1e-3).
+* Conduction between Dirichlet top and bottom wall nodes: T = C = y / H exactly,
+  Nu = Sh = 1 on both walls.
+* At t = 0 (interior at rest) every wall node holds the equilibrium of Eq. 20 at
+  the wall's velocity and its own porosity.
 * Sec. 3.2's claim on a convective cavity: at Le = 1 and equal wall data, the
   steady T and C coincide and Nu = Sh; the coupled equilibria of "model A"
   (Eqs. 30-32) break the equality.
@@ -207,6 +211,56 @@ def test_nee_couette_exact(oracle_mod, s_nu):
     psi = o.stream_function()
     np.testing.assert_allclose(psi, np.broadcast_to((U * y ** 2 / (2 * H))[:, None], psi.shape),
                                rtol=0, atol=2e-12)   # ny velocity errors of <= 1e-13 summed
+
+
+EX9 = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], float)
+EY9 = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], float)
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def _feq9(rho, rho0, eps, ux, uy, cs2=1.0 / 3.0):
+    """Eq. 20 in velocity space."""
+    eu = EX9 * ux + EY9 * uy
+    u2 = ux * ux + uy * uy
+    return W9 * (rho + rho0 * (eu / cs2 + eu ** 2 / (2 * eps * cs2 ** 2) - u2 / (2 * eps * cs2)))
+
+
+def test_nee_initial_wall_state_is_the_wall_equilibrium(oracle_mod):
+    """At t = 0 the interior is at rest (f = w_i rho0), so Eq. 33 leaves every wall node
+    with f^eq(rho0, u_w) at its own porosity: the lid velocity on the top row, corners
+    included (the top wall's u_w at a corner), rest elsewhere; checked against Eq. 20 in
+    velocity space with a porosity that varies from node to node."""
+    O = oracle_mod
+    nx, ny, U = 9, 7, 0.08
+    p = O.derive_lid(nx, ny, 100.0, 1e3, 1e-2, 0.6, 1.0, 2.0, 1.0, U0=U, nee=True)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    eps = 0.45 + 0.4 * (xx + 2 * yy) / (nx + 2 * ny)
+    o = O.Oracle(p, seed=3, noise=0.0, eps_field=eps)
+    f = o.get()[0]
+    for j in range(ny):
+        for i in range(nx):
+            if 0 < i < nx - 1 and 0 < j < ny - 1:
+                continue
+            u = U if j == ny - 1 else 0.0
+            np.testing.assert_allclose(f[:, j, i], _feq9(p.rho0, p.rho0, eps[j, i], u, 0.0),
+                                       rtol=0, atol=1e-15, err_msg=f"wall node ({i}, {j})")
+
+
+def test_nee_top_bottom_conduction_exact(oracle_mod):
+    """Dirichlet wall nodes at the bottom (T = C = 0) and top (T = C = 1), adiabatic
+    sides, no flow: T = C = y / H with H = ny - 1, and Nu = Sh = 1 on both walls with
+    the node stencil and L = ny - 1."""
+    O = oracle_mod
+    nx, ny = 6, 11
+    p = O.derive_lid(nx, ny, 10.0, 1e3, 1e-2, 0.7, 1.0, 1.5, 1.0, sigma=1.4, nee=True)
+    p.gbT = p.gbC = 0.0
+    p.uw[3][0] = 0.0       # the lid at rest
+    o = O.Oracle(p, seed=4, noise=0.1)
+    exact = np.broadcast_to((np.arange(ny) / (ny - 1))[:, None], (ny, nx))
+    fl = _run_to(o, exact, exact)
+    np.testing.assert_allclose(fl["T"], exact, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(fl["C"], exact, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(o.nusselt_sherwood_tb(), [1, 1, 1, 1], rtol=0, atol=1e-11)
 
 
 def _steady(O, p, tol=1e-11, chunk=2000, cap=150):

@@ -13,7 +13,10 @@ the lattice scheme.
   present and alpha_e does not depend on sigma (Eq. 29);
 * the implicit velocity definition Eq. 17 at every node of a running cavity;
 * the decoupling claim of Sec. 3.2: at Le = 1 the steady T and C coincide and
-  neither depends on sigma.
+  neither depends on sigma;
+* the state at t = 0 (the equilibria of Eqs. 20 and 28, or of model A's
+  Eqs. 30-31, at rest) gives back the T and C it was made from through Eq. 26,
+  also with a porosity that varies from node to node.
 """
 import numpy as np
 import pytest
@@ -266,3 +269,20 @@ def test_decoupling_steady_state_independent_of_sigma(oracle_mod):
         assert nush[0] > 1.05, "convection should raise Nu above conduction"
     assert np.abs(res[0.5] - res[1.0]).max() < 1e-8
     assert np.abs(res[2.0] - res[1.0]).max() < 1e-8
+
+
+@pytest.mark.parametrize("model_a", [False, True])
+@pytest.mark.parametrize("field", [False, True])
+def test_initial_state_holds_the_given_fields(oracle_mod, model_a, field):
+    O = oracle_mod
+    nx, ny = 11, 8
+    p = O.derive(nx, ny, 1e4, 1e-2, 0.55, 1.0, 2.0, 1.0, sigma=1.6)
+    if model_a:
+        O.to_model_a(p)
+    rng = np.random.default_rng(3)
+    T0, C0 = rng.uniform(0, 1, (ny, nx)), rng.uniform(0, 1, (ny, nx))
+    eps = rng.uniform(0.4, 0.9, (ny, nx)) if field else None
+    o = O.Oracle(p, seed=1, noise=0.0, T_init=T0, C_init=C0, eps_field=eps)
+    fl = o.fields()
+    np.testing.assert_allclose(fl["T"], T0, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(fl["C"], C0, rtol=0, atol=1e-15)

@@ -24,6 +24,7 @@ WALLS = "tests/test_oracle_walls.py"
 FIELD = "tests/test_oracle_porous_field.py"
 NEE = "tests/test_oracle_nee.py"
 DERIVE = "tests/test_oracle_derive.py"
+MODEL_A = "tests/test_model_a.py"
 
 # (what is planted, the correct expression, the mistaken one, the pins that must fail)
 MISTAKES = [
@@ -101,6 +102,36 @@ MISTAKES = [
     ("stream function with rectangles for trapezoids",
      "acc += 0.5 * (ux[(size_t)(j - 1) * nx + i] + ux[(size_t)j * nx + i]);",
      "acc += ux[(size_t)j * nx + i];", [NEE + "::test_nee_couette_exact"]),
+    ("model A's Dirichlet wall without its capacity factor",
+     "double kg = p->model_a ? p->sigma : 1.0, kh = p->model_a ? px.eps : 1.0;",
+     "double kg = 1.0, kh = 1.0;", [MODEL_A]),
+    ("model A's n_eq,3 without the capacity (Eqs. 30-31)",
+     "neq[3] = p->model_a ? (-4.0 + 5.0 * varpi) * cap * Phi", "neq[3] = p->model_a ? (-4.0 + 5.0 * varpi) * Phi",
+     [MODEL_A]),
+    ("model A's initial g_0 without sigma",
+     "s->g[x] = (1.0 - varpi) * p->sigma * T;", "s->g[x] = (1.0 - varpi) * T;",
+     [PHYS + "::test_initial_state_holds_the_given_fields"]),
+    ("initial h_0 with the scalar porosity in a porosity field",
+     "s->h[x] = eps_x * C - varpi * C;", "s->h[x] = p->eps * C - varpi * C;",
+     [PHYS + "::test_initial_state_holds_the_given_fields"]),
+    ("Nu length scale nx - 1 on the bottom wall (halfway walls)",
+     "nuB += ny * (-8.0 * p->Tw[2] + 9.0 * T0 - T1) / 3.0 / dT;",
+     "nuB += (ny - 1) * (-8.0 * p->Tw[2] + 9.0 * T0 - T1) / 3.0 / dT;", [WALLS + "::test_top_bottom_conduction_exact"]),
+    ("F_eps of the scalar porosity in a porosity field (Eq. 7)",
+     "        q.Feps = 1.75 / sqrt(150.0 * q.eps * q.eps * q.eps);   /* Eq. 7 */\n", "", [FIELD]),
+    ("permeability field ignored",
+     "if (s->K) q.K = s->K[x];", "if (0) q.K = s->K[x];", [FIELD]),
+    ("sign in the top-wall gradient with wall nodes",
+     "nuT += wi * L * (3.0 * t0[top] - 4.0 * t0[top - r] + t0[top - 2 * r]) / 2.0 / dT;",
+     "nuT += wi * L * (3.0 * t0[top] - 4.0 * t0[top - r] - t0[top - 2 * r]) / 2.0 / dT;",
+     [NEE + "::test_nee_top_bottom_conduction_exact"]),
+    ("corner nodes take the side wall's velocity",
+     "const int sv = dj ? (dj > 0 ? 2 : 3) : (di > 0 ? 0 : 1);",
+     "const int sv = di ? (di > 0 ? 0 : 1) : (dj > 0 ? 2 : 3);",
+     [NEE + "::test_nee_initial_wall_state_is_the_wall_equilibrium"]),
+    ("wall-node equilibrium at the interior node's porosity (Eq. 33)",
+     "meq9(&pb, of.rho, uwx, uwy, mb);", "meq9(&pf, of.rho, uwx, uwy, mb);",
+     [NEE + "::test_nee_initial_wall_state_is_the_wall_equilibrium"]),
 ]
 
 
