@@ -221,3 +221,12 @@ def test_splitmix64_definition(oracle_mod):
         vals = seq(seed, 40)
         for k in (0, 1, 17, 39):
             assert O.uniform(seed, k) == (vals[k] >> 11) * 2.0 ** -53
+
+    # the initial state (reading r8): T = T0 + a (2 u - 1), C = C0 + a (2 u' - 1) with u
+    # the output at key j nx + i and u' at key (ny + j) nx + i
+    nx, ny, a, seed = 5, 4, 0.03, 77
+    p = O.derive(nx, ny, 1e4, 1e-2, 0.7, 1.0, 2.0, 1.0, sigma=1.3)
+    fl = O.Oracle(p, seed=seed, noise=a).fields()
+    u = np.array([(v >> 11) * 2.0 ** -53 for v in seq(seed, 2 * nx * ny)]).reshape(2, ny, nx)
+    np.testing.assert_allclose(fl["T"], p.T0 + a * (2 * u[0] - 1), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(fl["C"], p.C0 + a * (2 * u[1] - 1), rtol=0, atol=1e-15)

@@ -98,6 +98,28 @@ def test_linear_conduction_exact(oracle_mod, zeta_a, cap):
     assert np.abs(fl["ux"]).max() < 1e-15
 
 
+def test_linear_conduction_with_distinct_wall_values(oracle_mod):
+    """T and C with different Dirichlet values (T: 1 | 0, C: 0.2 | 0.9): each is linear
+    between its own wall values, exactly."""
+    O = oracle_mod
+    nx, ny = 8, 3
+    p = O.derive(nx, ny, 1e4, 1e-2, 0.6, 1, 1.5, 1, sigma=1.4)
+    p.gbT = p.gbC = 0.0
+    for k in (1, 2):
+        p.zeta[k], p.eta[k] = 1.0, 0.8
+    p.Cw[0], p.Cw[1] = 0.2, 0.9
+    o = O.Oracle(p, seed=9, noise=0.3)
+    x = (np.arange(nx) + 0.5) / nx
+    eT, eC = 1.0 - x, 0.2 + 0.7 * x
+    for _ in range(40):
+        o.step(2000)
+        fl = o.fields()
+        if np.abs(fl["T"] - eT).max() < 1e-14 and np.abs(fl["C"] - eC).max() < 1e-14:
+            break
+    np.testing.assert_allclose(fl["T"], np.broadcast_to(eT, (ny, nx)), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(fl["C"], np.broadcast_to(eC, (ny, nx)), rtol=0, atol=1e-13)
+
+
 def _channel(O, ny, Feps, G=1e-5, eps=0.6, s_nu=1.0, Da=0.02, steps=None):
     """Fully developed flow along periodic x between no-slip walls at y = 0, H."""
     p = O.derive(4, ny, 1e4, 1e-2, eps, 1, 1, 0)

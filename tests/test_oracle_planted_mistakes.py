@@ -132,6 +132,57 @@ MISTAKES = [
     ("wall-node equilibrium at the interior node's porosity (Eq. 33)",
      "meq9(&pb, of.rho, uwx, uwy, mb);", "meq9(&pf, of.rho, uwx, uwy, mb);",
      [NEE + "::test_nee_initial_wall_state_is_the_wall_equilibrium"]),
+    ("C's anti-bounce-back with T's wall value",
+     "s->h2[opp[q] * n + x] = -hs[q] + 2.0 * wt_axis * kh * p->Cw[side];",
+     "s->h2[opp[q] * n + x] = -hs[q] + 2.0 * wt_axis * kh * p->Tw[side];",
+     [PHYS + "::test_linear_conduction_with_distinct_wall_values"]),
+    ("T's wall value taken from the opposite wall",
+     "s->g2[opp[q] * n + x] = -gs[q] + 2.0 * wt_axis * kg * p->Tw[side];",
+     "s->g2[opp[q] * n + x] = -gs[q] + 2.0 * wt_axis * kg * p->Tw[side ^ 1];", [PHYS]),
+    ("C's initial noise drawn at T's keys",
+     "p->C0 + noise * (2.0 * or_uniform(seed, n + x) - 1.0);",
+     "p->C0 + noise * (2.0 * or_uniform(seed, x) - 1.0);", [COLL + "::test_splitmix64_definition"]),
+    ("N^-1 transposed in the D2Q5 back-transform",
+     "for (int k = 0; k < 5; ++k) ds[i] += N5inv[i][k] * ns[k];",
+     "for (int k = 0; k < 5; ++k) ds[i] += N5inv[k][i] * ns[k];", [COLL]),
+    ("D2Q5 axis weights varpi / 5",
+     "double wt[5] = {1.0 - varpi, varpi / 4, varpi / 4, varpi / 4, varpi / 4};",
+     "double wt[5] = {1.0 - varpi, varpi / 5, varpi / 5, varpi / 5, varpi / 5};", [COLL]),
+    ("factor 2 under the root of Eq. 18",
+     "double den = l0 + sqrt(l0 * l0 + l1 * vmag);", "double den = l0 + sqrt(l0 * l0 + 2.0 * l1 * vmag);", [COLL]),
+    ("|v| for |u| in the Forchheimer force (Eq. 5)",
+     "double Fx = -eps * p->nu / p->K * ux - eps * p->Feps / sqrt(p->K) * umag * ux + eps * Gx;",
+     "double Fx = -eps * p->nu / p->K * ux - eps * p->Feps / sqrt(p->K) * vmag * ux + eps * Gx;", [COLL]),
+    ("sign of the solutal buoyancy (Eq. 6)",
+     "double Gy = p->gbT * (T - p->T0) + p->gbC * (C - p->C0);",
+     "double Gy = p->gbT * (T - p->T0) - p->gbC * (C - p->C0);", [COLL]),
+    ("eps dropped from m_eq,1 (Eq. 14)",
+     "meq[1] = -2.0 * rho + 3.0 * rho0 * u2 / eps;", "meq[1] = -2.0 * rho + 3.0 * rho0 * u2;", [COLL]),
+    ("eps dropped from m_eq,8 (Eq. 14)",
+     "meq[8] = rho0 * ux * uy / eps;", "meq[8] = rho0 * ux * uy;", [COLL]),
+    ("eps put into n_eq,1 (Eq. 24)",
+     "neq[1] = ux * Phi;", "neq[1] = ux * Phi / p->eps;", [COLL]),
+    ("C's source term from T's history",
+     "double XCx = Cux - hist[2], XCy = Cuy - hist[3];",
+     "double XCx = Cux - hist[0], XCy = Cuy - hist[1];", [COLL]),
+    ("zeta for eta in the concentration collision",
+     "collide_d2q5(p, p->eta, eps, o->C, ux, uy, XCx, XCy, h, hs);",
+     "collide_d2q5(p, p->zeta, eps, o->C, ux, uy, XCx, XCy, h, hs);", [COLL]),
+    ("C at x_ff through sigma (Eq. 26)",
+     "const double Tff = sgff / pff.sigma, Cff = shff / pff.eps;",
+     "const double Tff = sgff / pff.sigma, Cff = shff / pff.sigma;", [NEE + "::test_nee_dirichlet_conduction_exact"]),
+    ("x_ff = x_f in the gradient extrapolation",
+     "const size_t xff = (size_t)(j + 2 * dj) * nx + (i + 2 * di);",
+     "const size_t xff = (size_t)(j + dj) * nx + (i + di);", [NEE + "::test_convective_right_wall_exact"]),
+    ("a convective wall treated as Dirichlet",
+     "if (!(Bi[sd] > 0.0) && kind == OR_DIRICHLET) return W[sd];",
+     "if (kind == OR_DIRICHLET) return W[sd];", [NEE + "::test_convective_right_wall_exact"]),
+    ("sign in the right-wall gradient (halfway walls)",
+     "double dTdx_R = (8.0 * p->Tw[1] - 9.0 * Tr[nx - 1] + Tr[nx - 2]) / 3.0;",
+     "double dTdx_R = (8.0 * p->Tw[1] - 9.0 * Tr[nx - 1] - Tr[nx - 2]) / 3.0;", [PHYS]),
+    ("plain mean for the trapezoidal mean with wall nodes",
+     "const double wj = (j == 0 || j == ny - 1) ? 0.5 : 1.0;", "const double wj = 1.0;",
+     [NEE + "::test_nee_dirichlet_conduction_exact"]),
 ]
 
 
@@ -146,7 +197,7 @@ def _build(tmp, k, src):
 
 
 def _pins_fail(so, targets):
-    env = dict(os.environ, LBM_ORACLE_LIB=so, OMP_NUM_THREADS="2")
+    env = dict(os.environ, LBM_ORACLE_LIB=so, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", *targets, "-x", "-q", "-m", "not gpu",
                         "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True,
                        text=True, timeout=600)
@@ -160,7 +211,7 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
     for what, good, _, _ in MISTAKES:
         assert src.count(good) == 1, f"'{what}': the expression is not in the oracle exactly once"
     sos = [_build(str(tmp_path), k, src.replace(good, bad)) for k, (_, good, bad, _) in enumerate(MISTAKES)]
-    workers = max(1, min(4, os.cpu_count() or 1))
+    workers = max(1, min(8, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         results = list(ex.map(lambda a: _pins_fail(*a), [(so, m[3]) for so, m in zip(sos, MISTAKES)]))
     missed = [(m[0], out) for m, (rc, out) in zip(MISTAKES, results) if rc != 1]
