@@ -308,3 +308,31 @@ def test_initial_state_holds_the_given_fields(oracle_mod, model_a, field):
     fl = o.fields()
     np.testing.assert_allclose(fl["T"], T0, rtol=0, atol=1e-15)
     np.testing.assert_allclose(fl["C"], C0, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("model_a", [False, True])
+def test_scalar_content_changes_by_the_wall_link_fluxes(oracle_mod, model_a):
+    """Over one step the total sum g (= sum sigma T) changes only by what the D2Q5 links
+    carry through the walls: the collision conserves it (the source term of Eq. 27 has
+    no zeroth moment), streaming moves it, bounce-back on the adiabatic walls returns
+    it.  Through a Dirichlet wall, anti-bounce-back gives the entering population
+    g_in = -g*_out + 2 k w~ Phi_w (k = 1; model A: the capacity), so the net inflow of
+    a link is 2 g_in - 2 k w~ Phi_w, read from the state after the step.  Same for h."""
+    O = oracle_mod
+    nx, ny = 12, 9
+    p = O.derive(nx, ny, 5e4, 1e-2, 0.6, 1.0, 2.0, -0.5, sigma=1.3)
+    p.Cw[0], p.Cw[1] = 0.9, 0.15
+    if model_a:
+        O.to_model_a(p)
+    o = O.Oracle(p, seed=4, noise=0.05)
+    o.step(60)
+    _, g0, h0, _ = o.get()
+    o.step(1)
+    _, g1, h1, _ = o.get()
+    wt = p.varpi / 4
+    for a0, a1, W, cap in ((g0, g1, p.Tw, p.sigma), (h0, h1, p.Cw, p.eps)):
+        k = cap if model_a else 1.0
+        inflow = (2 * a1[1, :, 0] - 2 * k * wt * W[0]).sum() + (2 * a1[3, :, nx - 1] - 2 * k * wt * W[1]).sum()
+        change = a1.sum() - a0.sum()
+        assert abs(inflow) > 1e-6                       # the walls do carry something
+        assert abs(change - inflow) <= 1e-13 * abs(a1.sum()), (change, inflow)

@@ -180,6 +180,12 @@ MISTAKES = [
     ("sign in the right-wall gradient (halfway walls)",
      "double dTdx_R = (8.0 * p->Tw[1] - 9.0 * Tr[nx - 1] + Tr[nx - 2]) / 3.0;",
      "double dTdx_R = (8.0 * p->Tw[1] - 9.0 * Tr[nx - 1] - Tr[nx - 2]) / 3.0;", [PHYS]),
+    ("adiabatic wall reflecting h with a sign flip",
+     "s->h2[opp[q] * n + x] = hs[q];", "s->h2[opp[q] * n + x] = -hs[q];",
+     [PHYS + "::test_scalar_content_changes_by_the_wall_link_fluxes"]),
+    ("adiabatic wall reflecting g into the same direction",
+     "s->g2[opp[q] * n + x] = gs[q];", "s->g2[q * n + x] = gs[q];",
+     [PHYS + "::test_scalar_content_changes_by_the_wall_link_fluxes"]),
     ("plain mean for the trapezoidal mean with wall nodes",
      "const double wj = (j == 0 || j == ny - 1) ? 0.5 : 1.0;", "const double wj = 1.0;",
      [NEE + "::test_nee_dirichlet_conduction_exact"]),
