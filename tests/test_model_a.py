@@ -87,3 +87,32 @@ def test_model_a_equals_present_model_at_unit_capacities(oracle_mod):
     fa, fb = a.fields(), b.fields()
     for k in ("ux", "uy", "T", "C"):
         np.testing.assert_allclose(fa[k], fb[k], rtol=0, atol=1e-13)   # rounding order only
+
+
+@pytest.mark.parametrize("sigma,eps", [(0.6, 0.5), (1.8, 0.8)])
+def test_model_a_rates_give_the_same_diffusivities(oracle_mod, sigma, eps):
+    """Eq. 32: with model A's equilibria the D2Q5 diffusive flux is
+    sigma c_sT^2 (1/zeta_a - 1/2) grad T, so the rates re-derived for model A keep
+    alpha_e (and D_e) of the present model: a sine of T at rest decays as
+    exp(-alpha_e k^2 t / sigma), a sine of C as exp(-D_e k^2 t / eps)."""
+    O = oracle_mod
+    nx, ny = 128, 3
+    p = O.to_model_a(O.derive(nx, ny, 1e3, 1e-2, eps, 1.0, 2.0, 0.0, sigma=sigma))
+    p.periodic_x = p.periodic_y = 1
+    p.gbT = p.gbC = 0.0
+    x = np.arange(nx) + 0.5
+    kw = 2 * np.pi / nx
+    A = 0.1
+    field = np.broadcast_to(0.5 + A * np.sin(kw * x), (ny, nx)).copy()
+    o = O.Oracle(p, seed=1, noise=0.0, T_init=field, C_init=field)
+    nsteps = 3000
+    o.step(nsteps)
+    fl = o.fields()
+    for key, diff, cap in (("T", p.alpha_e, sigma), ("C", p.D_e, eps)):
+        row = fl[key][0] - 0.5
+        amp = np.abs((row * np.exp(-1j * kw * x)).sum() * 2 / nx)
+        rate, exact = -np.log(amp / A) / nsteps, diff * kw ** 2 / cap
+        assert exact * nsteps > 0.3                 # the wave has decayed measurably
+        # within the lattice's O(k^2) dispersion; a capacity factor missing from Eq. 32
+        # would be off by sigma or eps
+        assert abs(rate / exact - 1) < 1e-2, (key, rate, exact)
