@@ -757,6 +757,56 @@ void or_stream_function(const or_state* s, double* psi)
     free(ux);
 }
 
+/* ---- steady-state residual ---------------------------------------------------------
+ * The steady runs of Sec. 4 (Tables 1-5) stop when the fields no longer change.  The
+ * paper does not state its test; the reading taken is the relative change of the
+ * four fields over the last k steps,
+ *   r = max over phi in {u_x, u_y, T, C} of  max_x |phi_now(x) - phi_prev(x)| / max_x |phi_now(x)|,
+ * with T and C the absolute values of Eq. 26 and u from Eq. 18.  A field that is zero
+ * everywhere now contributes 0 if it did not change and +inf if it did.
+ * now, prev: planes [4][n] holding (u_x, u_y, T, C).  Returns 1 if a value of now is
+ * not finite (the run has diverged), else 0. */
+int or_residual_fields(long n, const double* now, const double* prev, double* r)
+{
+    int bad = 0;
+    double res = 0.0;
+    for (int q = 0; q < 4; ++q) {
+        const double* a = now + (size_t)q * n;
+        const double* b = prev + (size_t)q * n;
+        double dmax = 0.0, amax = 0.0;
+        for (long x = 0; x < n; ++x) {
+            if (!isfinite(a[x])) bad = 1;
+            const double d = fabs(a[x] - b[x]);
+            if (d > dmax) dmax = d;
+            if (fabs(a[x]) > amax) amax = fabs(a[x]);
+        }
+        double rq;
+        if (amax > 0.0)
+            rq = dmax / amax;
+        else
+            rq = dmax > 0.0 ? INFINITY : 0.0;
+        if (rq > res) res = rq;
+    }
+    *r = res;
+    return bad;
+}
+
+/* The residual of the current state against the fields an earlier call left in snap
+ * ([4][ny][nx]: u_x, u_y, T, C), which is then overwritten with the current fields.
+ * have_snap = 0: snap holds nothing yet and r = +inf.  Returns 1 if a current field
+ * value is not finite, else 0. */
+int or_residual(const or_state* s, double* snap, int have_snap, double* r)
+{
+    const size_t n = s->n;
+    double* now = (double*)malloc(4 * n * sizeof(double));
+    or_fields(s, now, now + n, now + 2 * n, now + 3 * n, NULL);
+    int bad = or_residual_fields((long)n, now, snap, r);
+    if (!have_snap) *r = INFINITY;
+    memcpy(snap, now, 4 * n * sizeof(double));
+    free(now);
+    return bad;
+}
+
 void or_get(const or_state* s, double* f, double* g, double* h, double* hist)
 {
     size_t n = s->n;

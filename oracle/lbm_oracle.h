@@ -22,6 +22,7 @@
  *     extrapolation and gradient extrapolation                Sec. 3.3, Eqs. 33-37
  *   - convective (Robin) walls                                 Sec. 4.2, Eq. 39
  *   - Nusselt / Sherwood numbers                               Sec. 4.1, Eq. 38
+ *   - steady-state residual (stopping test of the steady runs)  Sec. 4 (reading below)
  *   - parameter mapping from Ra, Pr, Le, Da, Ma                Sec. 4 and 4.1
  * Readings where the paper is silent (all stated again beside the code):
  *   - walls (default): no-slip halfway bounce-back for f; anti-bounce-back
@@ -43,6 +44,8 @@
  *     difference the paper suggests (Sec. 3.2), with the history initialised
  *     to T*u of the initial state, so the source vanishes at the first step.
  *   - initial noise: SplitMix64 (Steele, Lea & Flood 2014), see or_uniform().
+ *   - steady state: the paper states no test; the relative change of u_x, u_y,
+ *     T, C over the last k steps is taken (or_residual).
  *
  * Parity status: every function here is pinned by tests under tests/
  * (identities between the paper's moment- and velocity-space forms,
@@ -128,6 +131,16 @@ void or_nusselt_sherwood_tb(const or_state* s, double out[4]);
  * the trapezoidal rule up each column (from the wall node when nee, else from the
  * halfway wall half a spacing below the first node, where u = 0). */
 void or_stream_function(const or_state* s, double* psi);
+
+/* Steady-state residual (the stopping test of the steady runs of Sec. 4; the paper states
+ * none, the reading taken is): r = max over phi in {u_x, u_y, T, C} of
+ * max_x |phi_now - phi_prev| / max_x |phi_now| (absolute T and C; a field that is zero
+ * everywhere contributes 0 if unchanged, +inf otherwise).  now / prev are planes [4][n]
+ * of (u_x, u_y, T, C).  Returns 1 if a value of now is not finite, else 0. */
+int or_residual_fields(long n, const double* now, const double* prev, double* r);
+/* The same for the current state against snap ([4][ny][nx], the fields of an earlier
+ * call), which is replaced by the current fields; have_snap = 0 gives r = +inf. */
+int or_residual(const or_state* s, double* snap, int have_snap, double* r);
 
 /* Copy the distributions out / in, layout [q][ny][nx]; hist is [4][ny][nx] =
  * (T u_x, T u_y, C u_x, C u_y) at the previous collision. */

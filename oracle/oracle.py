@@ -87,6 +87,10 @@ def lib():
             L.or_nusselt_sherwood.argtypes = [C.c_void_p, dp]
             L.or_nusselt_sherwood_tb.argtypes = [C.c_void_p, dp]
             L.or_stream_function.argtypes = [C.c_void_p, dp]
+            L.or_residual_fields.argtypes = [C.c_long, dp, dp, dp]
+            L.or_residual_fields.restype = C.c_int
+            L.or_residual.argtypes = [C.c_void_p, dp, C.c_int, dp]
+            L.or_residual.restype = C.c_int
             L.or_get.argtypes = [C.c_void_p, dp, dp, dp, dp]
             L.or_set.argtypes = [C.c_void_p, dp, dp, dp, dp]
             L.or_collide_node.argtypes = [P, dp, dp, dp, dp, dp, dp, dp, dp]
@@ -168,6 +172,18 @@ def to_model_a(p: Params) -> Params:
     return p
 
 
+def residual_fields(now, prev):
+    """Steady-state residual of Sec. 4's steady runs (reading: the relative change of
+    (u_x, u_y, T, C)): now / prev are arrays [4, ...] of those fields.  Returns
+    (r, diverged)."""
+    a = np.ascontiguousarray(now, dtype=np.float64)
+    b = np.ascontiguousarray(prev, dtype=np.float64)
+    assert a.shape == b.shape and a.shape[0] == 4
+    r = C.c_double()
+    bad = lib().or_residual_fields(a.size // 4, _ptr(a), _ptr(b), C.byref(r))
+    return r.value, bool(bad)
+
+
 def set_threads(n: int) -> None:
     lib().or_set_threads(int(n))
 
@@ -227,6 +243,17 @@ class Oracle:
         psi = np.empty((self.ny, self.nx))
         lib().or_stream_function(self.h, _ptr(psi))
         return psi
+
+    def residual(self):
+        """Residual of the current fields against those of the previous call (+inf on
+        the first call); returns (r, diverged)."""
+        if not hasattr(self, "_snap"):
+            self._snap = np.zeros((4, self.ny, self.nx))
+            self._have_snap = 0
+        r = C.c_double()
+        bad = lib().or_residual(self.h, _ptr(self._snap), self._have_snap, C.byref(r))
+        self._have_snap = 1
+        return r.value, bool(bad)
 
     def get(self):
         shp = (self.ny, self.nx)

@@ -25,6 +25,7 @@ FIELD = "tests/test_oracle_porous_field.py"
 NEE = "tests/test_oracle_nee.py"
 DERIVE = "tests/test_oracle_derive.py"
 MODEL_A = "tests/test_model_a.py"
+RESID = "tests/test_oracle_residual.py"
 
 # (what is planted, the correct expression, the mistaken one, the pins that must fail)
 MISTAKES = [
@@ -186,6 +187,22 @@ MISTAKES = [
     ("adiabatic wall reflecting g into the same direction",
      "s->g2[opp[q] * n + x] = gs[q];", "s->g2[q * n + x] = gs[q];",
      [PHYS + "::test_scalar_content_changes_by_the_wall_link_fluxes"]),
+    ("residual against the earlier field's maximum",
+     "if (fabs(a[x]) > amax) amax = fabs(a[x]);", "if (fabs(b[x]) > amax) amax = fabs(b[x]);",
+     [RESID]),
+    ("residual without the concentration field",
+     "    for (int q = 0; q < 4; ++q) {\n        const double* a = now + (size_t)q * n;",
+     "    for (int q = 0; q < 3; ++q) {\n        const double* a = now + (size_t)q * n;", [RESID]),
+    ("absolute instead of relative change in the residual",
+     "            rq = dmax / amax;", "            rq = dmax;", [RESID]),
+    ("residual snapshot not replaced by the current fields",
+     "    memcpy(snap, now, 4 * n * sizeof(double));\n    free(now);",
+     "    if (!have_snap) memcpy(snap, now, 4 * n * sizeof(double));\n    free(now);", [RESID]),
+    ("residual of the first call taken against an empty snapshot",
+     "    if (!have_snap) *r = INFINITY;\n", "", [RESID]),
+    ("residual against the change's own maximum (deviations from the earlier field)",
+     "            if (fabs(a[x]) > amax) amax = fabs(a[x]);",
+     "            if (d > amax) amax = d;", [RESID]),
     ("plain mean for the trapezoidal mean with wall nodes",
      "const double wj = (j == 0 || j == ny - 1) ? 0.5 : 1.0;", "const double wj = 1.0;",
      [NEE + "::test_nee_dirichlet_conduction_exact"]),
