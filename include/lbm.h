@@ -424,8 +424,11 @@ const char* lbm_server_last_error(const lbm_server* s);
  * device array of LBM_NOALLOC_MAX_BLOCKS * 9 + 16 doubles (about 288 KiB), which
  * every GPU that loads the library holds until the process exits; any grid fits
  * (the blocks of the first pass share its slots).  The first call on each
- * device looks up the array's device address; make that first call before any
- * stream capture.  All calls share the array: each call clears it, then folds
+ * device looks up the array's device address and keeps it for the life of the
+ * process (a device reset, which unloads the library's device code, makes it
+ * stale); make that first call before any stream capture.  The call runs on the
+ * context's device whatever device the calling thread has current.  All calls
+ * share the array: each call clears it, then folds
  * into it; calls whose work overlaps on the GPU, from any context or stream,
  * race on it.  Synchronises the context's stream.  Errors as for
  * lbm_residual(), plus LBM_ERR_INVALID for NULL arguments. */

@@ -545,6 +545,22 @@ void or_destroy(or_state* s)
     free(s);
 }
 
+/* The initial T and C (reading r8: 1/2 plus noise * (2U - 1), U the SplitMix64 output
+ * with key (field * ny + j) * nx + i) of the window [x0, x0 + w) x [y0, y0 + h) of an
+ * nx x ny cavity, into T[h][w], C[h][w].  A window run of the oracle started from these
+ * reproduces the whole cavity's run within its dependence cone. */
+void or_noise_window(uint64_t seed, double noise, int nx, int ny, int x0, int y0, int w, int h,
+                     double* T, double* C)
+{
+    const uint64_t n = (uint64_t)nx * (uint64_t)ny;
+    for (int j = 0; j < h; ++j)
+        for (int i = 0; i < w; ++i) {
+            const uint64_t k = (uint64_t)(y0 + j) * (uint64_t)nx + (uint64_t)(x0 + i);
+            T[(size_t)j * w + i] = 0.5 + noise * (2.0 * or_uniform(seed, k) - 1.0);
+            C[(size_t)j * w + i] = 0.5 + noise * (2.0 * or_uniform(seed, n + k) - 1.0);
+        }
+}
+
 /* ---- one time step ------------------------------------------------------------- */
 
 void or_step(or_state* s, long nsteps)

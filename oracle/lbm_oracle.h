@@ -156,6 +156,11 @@ void or_collide_node(const or_params* p, const double f[9], const double g[5],
 /* The k-th SplitMix64 output of a generator seeded with `seed`, as a double in [0,1). */
 double or_uniform(uint64_t seed, uint64_t k);
 
+/* Initial T and C (1/2 + noise (2U - 1), U = or_uniform with key (field ny + j) nx + i)
+ * of the window [x0, x0 + w) x [y0, y0 + h) of an nx x ny cavity, into [h][w] arrays. */
+void or_noise_window(uint64_t seed, double noise, int nx, int ny, int x0, int y0, int w, int h,
+                     double* T, double* C);
+
 void or_set_threads(int n);
 int or_get_threads(void);
 

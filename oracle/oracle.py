@@ -97,6 +97,8 @@ def lib():
             L.or_uniform.argtypes = [C.c_uint64, C.c_uint64]
             L.or_uniform.restype = C.c_double
             L.or_set_threads.argtypes = [C.c_int]
+            L.or_noise_window.argtypes = [C.c_uint64, C.c_double, C.c_int, C.c_int, C.c_int,
+                                          C.c_int, C.c_int, C.c_int, dp, dp]
             L.or_get_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -182,6 +184,16 @@ def residual_fields(now, prev):
     r = C.c_double()
     bad = lib().or_residual_fields(a.size // 4, _ptr(a), _ptr(b), C.byref(r))
     return r.value, bool(bad)
+
+
+def noise_window(seed, noise, nx, ny, x0, y0, w, h):
+    """Initial (T, C) of the window [x0, x0 + w) x [y0, y0 + h) of an nx x ny cavity with
+    the seeded noise (the keys of the whole cavity), as [h][w] arrays."""
+    T = np.empty((h, w))
+    Cc = np.empty((h, w))
+    lib().or_noise_window(C.c_uint64(seed), float(noise), int(nx), int(ny), int(x0), int(y0),
+                          int(w), int(h), _ptr(T), _ptr(Cc))
+    return T, Cc
 
 
 def set_threads(n: int) -> None:

@@ -278,17 +278,6 @@ cudaError_t run_init(lbm_ctx* c, const InitSpec& I) {
 
 const void* cur_buf(const lbm_ctx* c) { return c->layout == LBM_AB_PULL ? c->buf[c->cur] : c->buf[0]; }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-        else prev = -1;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
 // (Re)initialise the state at t = 0 from host T / C fields or from the noise.
 lbm_status do_init(lbm_ctx* c, const double* T_host, const double* C_host, uint64_t seed,
                    double noise) {

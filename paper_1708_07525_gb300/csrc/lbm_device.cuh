@@ -123,7 +123,7 @@ template <> struct Store<__half> {
 
 // Store one of a node's populations: stochastic rounding for 16-bit storage when
 // sr is set (see sr_node).  The random bits come from a per-node linear
-// congruential stream (Knuth's MMIX constants) seeded by node_seed(); only its high
+// congruential stream (the 32-bit constants of Numerical Recipes) seeded by node_seed(); only its high
 // 16 bits are used, which is enough for rounding decisions and costs one
 // multiply-add per value.
 template <typename S, typename R>

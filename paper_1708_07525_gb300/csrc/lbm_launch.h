@@ -104,6 +104,22 @@ inline dim3 residual_grid(const Geom& G) {
 // reduces the slots.
 constexpr int RES_SLOTS = 4096;
 
+// Makes `dev` the calling thread's current device for the guard's lifetime and
+// restores the previous one afterwards (every entry point that touches a context's
+// device state holds one).
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
 // Kernel constants of a cavity from its lattice parameters (lbm_api.cu);
 // stochastic rounding of 16-bit stores is enabled (Coef::sr = 1).
 template <typename R>

@@ -33,19 +33,16 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 double* g_ptr[MAX_DEVICES] = {};
 
-// Device address of the scratch array on `dev`, looked up once per device with that
-// device current.  This happens on the first call on each device, so that first call
-// must not come while a stream is being captured.
+// Device address of the scratch array on `dev`, looked up once per device; the caller
+// has made `dev` current.  This happens on the first call on each device, so that first
+// call must not come while a stream is being captured.  The address is kept for the
+// life of the process: a device reset (which unloads the module) makes it stale.
 cudaError_t scratch_for_device(int dev, double** out) {
     if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_ptr[dev]) {
-        int prev = -1;
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
         double* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress((void**)&p, noalloc_scratch);
-        if (prev != dev && prev >= 0) cudaSetDevice(prev);
         if (e != cudaSuccess) return e;
         g_ptr[dev] = p;
     }
@@ -83,6 +80,9 @@ lbm_status lbm_residual_noalloc(lbm_ctx* ctx, double* snapshot, int have_snapsho
     CtxView v;
     if (!ctx || !snapshot || !r || !lbm_ctx_view(ctx, &v))
         return fail(ctx, LBM_ERR_INVALID, "ctx, snapshot and r must be non-NULL");
+    // the context's device for the whole call: the symbol lookup, the launches on the
+    // context's stream and the copy all belong to it
+    DeviceGuard dg(v.device);
     double* scratch = nullptr;
     cudaError_t e = scratch_for_device(v.device, &scratch);
     if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, "cudaGetSymbolAddress: ", cudaGetErrorString(e));

@@ -230,3 +230,7 @@ def test_splitmix64_definition(oracle_mod):
     u = np.array([(v >> 11) * 2.0 ** -53 for v in seq(seed, 2 * nx * ny)]).reshape(2, ny, nx)
     np.testing.assert_allclose(fl["T"], p.T0 + a * (2 * u[0] - 1), rtol=0, atol=1e-15)
     np.testing.assert_allclose(fl["C"], p.C0 + a * (2 * u[1] - 1), rtol=0, atol=1e-15)
+    # a window of a larger cavity takes the whole cavity's keys
+    T, Cw = O.noise_window(seed, a, nx, ny, 1, 2, 3, 2)
+    np.testing.assert_array_equal(T, p.T0 + a * (2 * u[0][2:4, 1:4] - 1))
+    np.testing.assert_array_equal(Cw, p.C0 + a * (2 * u[1][2:4, 1:4] - 1))

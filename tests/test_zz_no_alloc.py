@@ -54,3 +54,34 @@ def test_noalloc_takes_grids_beyond_its_scratch_blocks():
     assert np.isfinite(r_ref) and r_ref > 0
     assert abs(r_new - r_ref) <= 1e-12 * r_ref, (r_new, r_ref)
     cav.close()
+
+
+def test_noalloc_reports_non_finite_fields_and_clears_its_flag():
+    """A NaN in the initial T (made on the host) gives ERR_DIVERGED from the shared scratch's
+    flag slot; the next call, on a healthy cavity, clears the slots and returns a finite r
+    equal to lbm_residual's."""
+    import torch
+    n = 16
+    T = np.full((n, n), 0.5)
+    T[8, 8] = np.nan
+    bad = lbm.Cavity(n, n, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0, precision="f32", T_init=T,
+                     C_init=np.full((n, n), 0.5))
+    snap_bad = torch.zeros(4 * n * n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    bad.step(50)
+    with pytest.raises(lbm.LbmError) as ei:
+        bad.residual_noalloc(snap_bad.data_ptr(), False)
+    assert ei.value.status == lbm.ERR_DIVERGED
+    bad.close()
+    good = lbm.Cavity(n, n, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0, precision="f32", seed=3, noise=0.02)
+    snap = torch.zeros(4 * n * n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    good.step(40)
+    good.residual()
+    good.residual_noalloc(snap.data_ptr(), False)
+    good.step(30)
+    r_ref = good.residual()
+    r_new = good.residual_noalloc(snap.data_ptr(), True)
+    assert np.isfinite(r_new) and r_new > 0
+    assert abs(r_new - r_ref) <= 1e-12 * r_ref, (r_new, r_ref)
+    good.close()
