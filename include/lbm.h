@@ -263,8 +263,12 @@ lbm_status lbm_residual(lbm_ctx* ctx, double* r);
 
 /* Checkpoint of the full state (distributions, history, time, parameters).
  * lbm_save with buf == NULL stores the size needed in *len.  lbm_load
- * requires a checkpoint of a context with the same grid, precision and
- * layout.  Both synchronise the stream. */
+ * requires a checkpoint of a context with the same grid and layout; a
+ * checkpoint of another storage precision is converted on the host: each
+ * stored deviation (f_i - f_i^eq(rho0, 0) etc., Eqs. 20, 28) and history value
+ * is taken to FP64 and stored in this context's precision (exact when
+ * widening, e.g. an FP32 state polished further in FP64; rounded to nearest
+ * when narrowing).  Both synchronise the stream. */
 lbm_status lbm_save(lbm_ctx* ctx, void* buf, size_t* len);
 lbm_status lbm_load(lbm_ctx* ctx, const void* buf, size_t len);
 

@@ -119,6 +119,7 @@ Coef<R> make_coef(const lbm_params& P) {
 }
 template Coef<float> make_coef<float>(const lbm_params&);
 template Coef<double> make_coef<double>(const lbm_params&);
+template Coef<f2> make_coef<f2>(const lbm_params&);
 }  // namespace lbm
 
 namespace {
@@ -179,6 +180,7 @@ struct lbm_ctx {
     int device = 0;
     Coef<double> cd{};
     Coef<float> cf{};
+    Coef<f2> cp{};                  // 16-bit storage: cf as pairs (two nodes per thread)
     LaunchCfg L{};
     int graph_chunk = 0;
     bool round_nearest = false;     // 16-bit storage: nearest-even instead of stochastic
@@ -585,6 +587,8 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
     c->cf = make_coef<float>(c->P);
     c->round_nearest = O.round_nearest != 0;
     c->cf.sr = c->round_nearest ? 0 : 1;
+    c->cp = make_coef<f2>(c->P);
+    c->cp.sr = c->cf.sr;
     int bx = O.block_x, by = O.block_y;
     if (bx == 0) bx = nx >= 128 ? 128 : 32;
     if (by == 0) by = bx >= 128 ? 1 : 128 / bx;
@@ -599,6 +603,7 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
     c->L.by = by;
     c->L.stream = c->stream;
     c->L.aux = nullptr;
+    c->L.pair = (c->prec == LBM_BF16 || c->prec == LBM_F16) ? &c->cp : nullptr;
     // a second stream lets the small ring launch of a split step run beside the inner one;
     // without it both go to the context's stream
     if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) == cudaSuccess &&
@@ -925,6 +930,27 @@ lbm_status lbm_residual(lbm_ctx* c, double* r) {
 
 // Checkpoint layout: header, then the 19 state planes, then the 4 history planes.
 namespace {
+// A stored deviation as FP64: element k of a state array of precision prec (FP16 holds
+// the deviation scaled by 2^12), and the reverse (rounded to nearest for narrower types).
+double decode_value(int prec, const char* base, size_t k) {
+    switch (prec) {
+        case LBM_F64: return ((const double*)base)[k];
+        case LBM_F32: return (double)((const float*)base)[k];
+        case LBM_BF16: return (double)__bfloat162float(((const __nv_bfloat16*)base)[k]);
+        default: return (double)__half2float(((const __half*)base)[k]) / 4096.0;
+    }
+}
+void encode_value(int prec, char* base, size_t k, double v) {
+    switch (prec) {
+        case LBM_F64: ((double*)base)[k] = v; break;
+        case LBM_F32: ((float*)base)[k] = (float)v; break;
+        case LBM_BF16: ((__nv_bfloat16*)base)[k] = __float2bfloat16_rn((float)v); break;
+        default: ((__half*)base)[k] = __float2half_rn((float)(v * 4096.0)); break;
+    }
+}
+}  // namespace
+
+namespace {
 struct CkptHeader {
     char magic[8];
     int32_t version, nx, ny, prec, layout, pitch;
@@ -972,7 +998,6 @@ lbm_status lbm_load(lbm_ctx* c, const void* buf, size_t len) {
         set_global_error("lbm_load: NULL argument");
         return LBM_ERR_INVALID;
     }
-    const size_t need = sizeof(CkptHeader) + c->state_bytes() + c->hist_bytes();
     CkptHeader h;
     if (len < sizeof h) return c->fail(LBM_ERR_INVALID, "lbm_load: truncated checkpoint");
     std::memcpy(&h, buf, sizeof h);
@@ -982,22 +1007,69 @@ lbm_status lbm_load(lbm_ctx* c, const void* buf, size_t len) {
         return c->fail(LBM_ERR_INVALID, "lbm_load: checkpoint parameters: %s", bad);
     if (h.P.nee && c->layout != LBM_AB_PULL)
         return c->fail(LBM_ERR_INVALID, "lbm_load: walls with nodes on them need the two-buffer layout");
-    if (h.nx != c->G.nx || h.ny != c->G.ny || h.prec != c->prec || h.layout != c->layout ||
-        h.pitch != c->G.pitch || len < need)
+    if (h.nx != c->G.nx || h.ny != c->G.ny || h.layout != c->layout)
         return c->fail(LBM_ERR_INVALID, "lbm_load: checkpoint does not match this context");
+    if (h.prec < LBM_F64 || h.prec > LBM_F16)
+        return c->fail(LBM_ERR_INVALID, "lbm_load: checkpoint of unknown precision %d", h.prec);
+    const size_t src_esz = storage_size(h.prec), src_rsz = h.prec == LBM_F64 ? 8 : 4;
+    const size_t src_plane = (size_t)h.ny * (size_t)h.pitch;
+    const size_t src_state = (size_t)NQ * src_plane * src_esz, src_hist = 4 * src_plane * src_rsz;
+    if (h.pitch < h.nx || len < sizeof h + src_state + src_hist)
+        return c->fail(LBM_ERR_INVALID, "lbm_load: truncated checkpoint");
     DeviceGuard dg(c->device);
     // the two-buffer layout keeps the state in buffer (t mod 2), which the captured graph relies on
     const int slot = c->layout == LBM_AB_PULL ? (int)(h.t & 1) : 0;
     const char* p = (const char*)buf + sizeof h;
-    cudaError_t e = cudaMemcpyAsync(c->buf[slot], p, c->state_bytes(), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->hist, p + c->state_bytes(), c->hist_bytes(), cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e;
+    if (h.prec == c->prec && h.pitch == c->G.pitch) {
+        e = cudaMemcpyAsync(c->buf[slot], p, c->state_bytes(), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->hist, p + c->state_bytes(), c->hist_bytes(), cudaMemcpyHostToDevice,
+                                c->stream);
+    } else {
+        // another storage precision: every stored deviation and history value is decoded
+        // to FP64 and encoded in this context's precision (exact when widening, rounded to
+        // nearest when narrowing), row by row into this context's row pitch
+        std::vector<char> st;
+        try {
+            st.assign(c->state_bytes() + c->hist_bytes(), 0);
+        } catch (...) {
+            return c->fail(LBM_ERR_NOMEM, "lbm_load: no host memory to convert the checkpoint");
+        }
+        const size_t plane = c->G.plane;
+        for (int q = 0; q < NQ; ++q)
+            for (int j = 0; j < h.ny; ++j)
+                for (int i = 0; i < h.nx; ++i) {
+                    const size_t a = (size_t)q * src_plane + (size_t)j * h.pitch + i;
+                    const size_t b = (size_t)q * plane + (size_t)j * c->G.pitch + i;
+                    encode_value(c->prec, st.data(), b, decode_value(h.prec, p, a));
+                }
+        const char* ph = p + src_state;
+        char* dh = st.data() + c->state_bytes();
+        for (int k = 0; k < 4; ++k)
+            for (int j = 0; j < h.ny; ++j)
+                for (int i = 0; i < h.nx; ++i) {
+                    const size_t a = (size_t)k * src_plane + (size_t)j * h.pitch + i;
+                    const size_t b = (size_t)k * plane + (size_t)j * c->G.pitch + i;
+                    const double v = src_rsz == 8 ? ((const double*)ph)[a] : (double)((const float*)ph)[a];
+                    if (c->rsz == 8)
+                        ((double*)dh)[b] = v;
+                    else
+                        ((float*)dh)[b] = (float)v;
+                }
+        e = cudaMemcpyAsync(c->buf[slot], st.data(), c->state_bytes(), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->hist, dh, c->hist_bytes(), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // before st is released
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return c->cuda_fail(e, "lbm_load");
     c->P = h.P;
     c->cd = make_coef<double>(c->P);
     c->cf = make_coef<float>(c->P);
     c->cf.sr = c->round_nearest ? 0 : 1;
+    c->cp = make_coef<f2>(c->P);
+    c->cp.sr = c->cf.sr;
     c->cd.poro = (c->poro && c->rsz == 8) ? (const double*)c->poro : nullptr;
     c->cf.poro = (c->poro && c->rsz == 4) ? (const float*)c->poro : nullptr;
     if (c->graph) {   // constants are baked into the captured launches

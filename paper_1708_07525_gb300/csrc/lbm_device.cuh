@@ -12,6 +12,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbm {
 
 // D2Q9 velocities (Eq. 8), same ordering as the paper; D2Q5 uses q = 0..4.
@@ -158,6 +160,54 @@ __device__ __forceinline__ uint32_t node_seed(size_t node, R a, R b) {
     const uint32_t ia = __float_as_uint((float)a), ib = __float_as_uint((float)b);
     return mix32(ia ^ mix32(ib ^ mix32((uint32_t)node ^ (uint32_t)(node >> 32) * 0x27D4EB2Fu)));
 }
+
+// ---- two nodes per thread ----------------------------------------------------------
+// f2: the FP32 values of one quantity at two x-adjacent nodes, computed with the packed
+// FP32x2 instructions of sm_100 and later (one add, multiply or fused multiply-add for
+// both nodes).  Products are kept unevaluated (f2m) until they meet an addition or a
+// subtraction, which then becomes one fused multiply-add, as a compiler contracts
+// a * b + c in scalar code.  Division and square root act per component.  The scalar
+// collision and macroscopic code (collide, macro) is instantiated with R = f2.
+struct f2 {
+    float2 v;
+    f2() = default;
+    __host__ __device__ f2(float2 a) : v(a) {}
+    template <typename T, typename std::enable_if<std::is_arithmetic<T>::value, int>::type = 0>
+    __host__ __device__ explicit f2(T s) : v(make_float2((float)s, (float)s)) {}
+};
+#ifdef __CUDACC__
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+struct f2m {
+    float2 a, b;
+    __device__ __forceinline__ operator f2() const { return f2(__fmul2_rn(a, b)); }
+};
+__device__ __forceinline__ f2m operator*(f2 a, f2 b) { return f2m{a.v, b.v}; }
+__device__ __forceinline__ f2m operator*(f2m a, f2 b) { return f2m{f2(a).v, b.v}; }
+__device__ __forceinline__ f2m operator*(f2 a, f2m b) { return f2m{a.v, f2(b).v}; }
+__device__ __forceinline__ f2m operator*(f2m a, f2m b) { return f2m{f2(a).v, f2(b).v}; }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) {
+    return f2(__ffma2_rn(b.v, make_float2(-1.0f, -1.0f), a.v));   // round(a - b) exactly
+}
+__device__ __forceinline__ f2 operator+(f2m p, f2 c) { return f2(__ffma2_rn(p.a, p.b, c.v)); }
+__device__ __forceinline__ f2 operator+(f2 c, f2m p) { return f2(__ffma2_rn(p.a, p.b, c.v)); }
+__device__ __forceinline__ f2 operator-(f2 c, f2m p) { return f2(__ffma2_rn(neg2(p.a), p.b, c.v)); }
+__device__ __forceinline__ f2 operator-(f2m p, f2 c) { return f2(__ffma2_rn(p.a, p.b, neg2(c.v))); }
+__device__ __forceinline__ f2 operator+(f2m p, f2m q) { return f2(__ffma2_rn(p.a, p.b, f2(q).v)); }
+__device__ __forceinline__ f2 operator-(f2m p, f2m q) {
+    return f2(__ffma2_rn(neg2(q.a), q.b, f2(p).v));
+}
+__device__ __forceinline__ f2 operator-(f2 a) { return f2(neg2(a.v)); }
+__device__ __forceinline__ f2 operator-(f2m p) { return f2m{neg2(p.a), p.b}; }
+__device__ __forceinline__ f2& operator+=(f2& a, f2 b) { return a = a + b; }
+__device__ __forceinline__ f2& operator-=(f2& a, f2 b) { return a = a - b; }
+__device__ __forceinline__ f2& operator+=(f2& a, f2m b) { return a = a + b; }
+__device__ __forceinline__ f2& operator-=(f2& a, f2m b) { return a = a - b; }
+__device__ __forceinline__ f2 operator/(f2 a, f2 b) { return f2(make_float2(a.v.x / b.v.x, a.v.y / b.v.y)); }
+template <> __device__ __forceinline__ f2 sqrt_(f2 x) {
+    return f2(make_float2(sqrtf(x.v.x), sqrtf(x.v.y)));
+}
+#endif
 
 // Compute type for a storage type: FP64 stays FP64, everything else is FP32.
 template <typename S> struct Real { using type = float; };

@@ -47,6 +47,9 @@ struct LaunchCfg {
     // aux == nullptr: both launches go to `stream`.
     cudaStream_t aux;
     cudaEvent_t fork, join;
+    // 16-bit storage: the cavity's constants as pairs for the two-nodes-per-thread
+    // kernels (lbm_pair.cuh); nullptr -> the one-node kernels
+    const Coef<f2>* pair;
 };
 
 // Stream for the ring launch of a split step (after forking from L.stream).

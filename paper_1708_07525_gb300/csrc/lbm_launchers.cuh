@@ -4,6 +4,7 @@
 #include <type_traits>
 
 #include "lbm_kernels.cuh"
+#include "lbm_pair.cuh"
 
 namespace lbm {
 
@@ -28,11 +29,43 @@ cudaError_t launch_init(void* buf, void* hist, const Geom& G, const Coef<typenam
     return cudaGetLastError();
 }
 
+// Grids of the two-nodes-per-thread kernels (lbm_pair.cuh); false if the cavity does
+// not take them (too small, or too many rows for one launch).
+inline bool pair_grid_ab(const Geom& G, dim3& gr) {
+    const int np = inner_pairs(G.nx), rows = G.ny - 2;
+    if (G.nx < 8 || rows < 1 || np < 1) return false;
+    gr = dim3((unsigned)((np + PAIR_BX - 1) / PAIR_BX), (unsigned)((rows + PAIR_BY - 1) / PAIR_BY), 1);
+    return gr.y <= 65535u;
+}
+inline bool pair_grid_aa_even(const Geom& G, dim3& gr) {
+    if (G.nx & 1) return false;
+    gr = dim3((unsigned)((G.nx / 2 + PAIR_BX - 1) / PAIR_BX), (unsigned)((G.ny + PAIR_BY - 1) / PAIR_BY), 1);
+    return gr.y <= 65535u;
+}
+
 template <typename S>
 cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G,
                            const Coef<typename Real<S>::type>& c, const LaunchCfg& L) {
     using R = typename Real<S>::type;
     dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
+    if constexpr (Store<S>::kLow) {
+        dim3 gp;
+        if (L.pair && !c.nee && !c.poro && !c.moving && pair_grid_ab(G, gp)) {
+            // inner column pairs two nodes per thread, the edge set one node per thread
+            // on the second stream (disjoint destinations)
+            cudaStream_t rs;
+            cudaError_t e = ring_fork(L, &rs);
+            if (e != cudaSuccess) return e;
+            const long long ne = edge_count(G);
+            step_ab_edge_kernel<S><<<(unsigned)((ne + 127) / 128), 128, 0, rs>>>(
+                (const S*)src, (S*)dst, (float*)hist, G, c);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            step_ab_pair_kernel<S><<<gp, dim3(PAIR_BX, PAIR_BY), 0, L.stream>>>(
+                (const S*)src, (S*)dst, (float*)hist, G, *L.pair);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            return ring_join(L);
+        }
+    }
     if (c.nee) {
         // the ring of wall nodes: the rebuild (Sec. 3.3); inner nodes: the plain pull
         cudaStream_t rs;
@@ -82,6 +115,26 @@ cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
     using R = typename Real<S>::type;
     dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
     const bool ext = c.poro || c.moving;
+    if constexpr (Store<S>::kLow) {
+        dim3 gp, ge;
+        if (L.pair && !ext && pair_grid_ab(G, gp) && pair_grid_aa_even(G, ge)) {
+            const dim3 pb(PAIR_BX, PAIR_BY);
+            if (!odd) {
+                step_aa_even_pair_kernel<S><<<ge, pb, 0, L.stream>>>((S*)buf, (float*)hist, G, *L.pair);
+                return cudaGetLastError();
+            }
+            cudaStream_t rs;
+            cudaError_t e = ring_fork(L, &rs);
+            if (e != cudaSuccess) return e;
+            const long long ne = edge_count(G);
+            step_aa_odd_edge_kernel<S><<<(unsigned)((ne + 127) / 128), 128, 0, rs>>>(
+                (S*)buf, (float*)hist, G, c);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            step_aa_odd_pair_kernel<S><<<gp, pb, 0, L.stream>>>((S*)buf, (float*)hist, G, *L.pair);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            return ring_join(L);
+        }
+    }
     if (odd && G.nx >= 3 && G.ny >= 3) {
         // the ring of outermost nodes beside the inner nodes (no wall logic); the two
         // launches touch disjoint locations

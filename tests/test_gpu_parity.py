@@ -147,6 +147,40 @@ def test_checkpoint_resume_bitwise(layout):
         assert np.array_equal(fa[k], fb[k]), k
 
 
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_checkpoint_across_precisions(layout):
+    """A checkpoint loads into a context of another storage precision: widening is exact
+    (FP32 -> FP64 -> FP32 gives back the FP32 state bit for bit; a 16-bit state read in FP32
+    gives the same fields), and the widened state steps on in the new precision."""
+    spec = SMALL[2]
+    args = dict(layout=layout, seed=spec.seed, noise=spec.noise)
+    a = lbm.Cavity(*spec.args(), precision="f32", **args)
+    a.step(333)
+    blob = a.save()
+    b = lbm.Cavity(*spec.args(), precision="f64", **args)
+    b.load(blob)
+    assert b.t == 333
+    c = lbm.Cavity(*spec.args(), precision="f32", **args)
+    c.load(b.save())
+    fa, fb, fc = a.fields(), b.fields(), c.fields()
+    for k in KEYS:
+        assert np.array_equal(fa[k], fc[k]), k
+        assert rel_l2(fb[k], fa[k]) <= 1e-6, k
+    a.step(500)
+    b.step(500)
+    fa, fb = a.fields(), b.fields()
+    for k in KEYS:
+        assert rel_l2(fa[k], fb[k]) <= 1e-5, k
+    for prec in ("bf16", "f16"):
+        h = lbm.Cavity(*spec.args(), precision=prec, **args)
+        h.step(101)
+        w = lbm.Cavity(*spec.args(), precision="f32", **args)
+        w.load(h.save())
+        fh, fw = h.fields(), w.fields()
+        for k in KEYS:
+            assert np.array_equal(fh[k], fw[k]), (prec, k)
+
+
 def test_user_initial_fields_match_oracle(oracle_mod):
     from paper_1708_07525_gb300.workloads import random_fields
     spec = SMALL[2]
