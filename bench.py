@@ -356,6 +356,171 @@ def run_ours(args):
     return 0
 
 
+def run_slab(args):
+    """One cavity of n x (n * N) nodes cut into N slabs of n rows, one per rank (weak
+    scaling: every rank advances n^2 nodes).  After every time step the ranks swap the
+    five populations per column that cross each cut (lbm_halo_export / _import) with
+    NCCL send / receive (--comm nccl, one GPU per rank) or through the host over gloo
+    (--comm gloo).  One bench step = 100 time steps with their exchanges, then the FP64
+    Nu / Sh (row means combined over ranks) and the residual (maxima combined)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_setup(args.gpus)
+    dev_index = local if args.comm == "nccl" else args.device
+    torch.cuda.set_device(dev_index)
+    if world > 1:
+        if args.comm == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", dev_index))
+        else:
+            dist.init_process_group("gloo")
+    from paper_1708_07525_gb300 import lbm
+    from paper_1708_07525_gb300.workloads import throughput_cavity
+    n = args.size
+    spec = throughput_cavity(n)
+    p = lbm.lbm_derive_params(n, n * world, spec.Ra, spec.Da, spec.eps, spec.Pr, spec.Le, spec.N,
+                              spec.J, spec.sigma, 0.0, spec.varpi)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    slab = lbm.Cavity(params=p, slab=(rank * n, n), precision=args.precision, seed=spec.seed,
+                      noise=spec.noise, stream=stream.cuda_stream, block=(args.bx, args.by))
+    nb = slab.halo_bytes()
+    dev_faces = {k: torch.empty(nb, dtype=torch.uint8, device="cuda")
+                 for k in ("down_out", "up_out", "below_in", "above_in")}
+    host = args.comm != "nccl"
+    host_faces = {k: torch.empty(nb, dtype=torch.uint8).pin_memory() for k in dev_faces} if host else {}
+    lo, hi = rank > 0, rank < world - 1
+
+    def exchange():
+        if world == 1:
+            return
+        if lo:
+            slab.halo_export(0, dev_faces["down_out"].data_ptr())
+        if hi:
+            slab.halo_export(1, dev_faces["up_out"].data_ptr())
+        bufs = dev_faces
+        if host:
+            stream.synchronize()
+            for k in ("down_out", "up_out"):
+                host_faces[k].copy_(dev_faces[k])
+            bufs = host_faces
+        ops = []
+        if lo:
+            ops += [dist.P2POp(dist.isend, bufs["down_out"], rank - 1),
+                    dist.P2POp(dist.irecv, bufs["below_in"], rank - 1)]
+        if hi:
+            ops += [dist.P2POp(dist.isend, bufs["up_out"], rank + 1),
+                    dist.P2POp(dist.irecv, bufs["above_in"], rank + 1)]
+        for r in dist.batch_isend_irecv(ops):
+            r.wait()
+        if host:
+            for k in ("below_in", "above_in"):
+                dev_faces[k].copy_(host_faces[k], non_blocking=True)
+        if lo:
+            slab.halo_import(0, dev_faces["below_in"].data_ptr())
+        if hi:
+            slab.halo_import(1, dev_faces["above_in"].data_ptr())
+
+    k = STEPS_PER_BENCH_STEP
+
+    def bench_step():
+        for _ in range(k):
+            slab.step(1)
+            exchange()
+        nush = torch.tensor(slab.nusselt_sherwood() * n, dtype=torch.float64)
+        parts = torch.tensor(slab.residual_parts(), dtype=torch.float64)
+        if world > 1:
+            if not host:
+                nush, parts = nush.cuda(), parts.cuda()
+            dist.all_reduce(nush)
+            dist.all_reduce(parts, op=dist.ReduceOp.MAX)
+        nush = (nush / (n * world)).cpu().numpy()
+        parts = parts.cpu().numpy()
+        return nush, max(d / a if a > 0 else float("inf") for d, a in zip(parts[:4], parts[4:]))
+
+    for _ in range(args.warmup):
+        bench_step()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(dev_index) as clk:
+        t0 = time.perf_counter()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for _ in range(args.steps):
+            nush, r = bench_step()
+        stop.record(stream)
+        torch.cuda.synchronize()
+        wall_s = time.perf_counter() - t0
+    barrier()
+    total_ms = max_over_ranks(start.elapsed_time(stop), device="cuda" if not host else None)
+    value = aggregate_value(n * n * k * args.steps, total_ms / 1e3, world) / 1e9
+    line = {
+        "metric": METRIC, "mode": "slab", "value": value, "unit": "GLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"porous cavity {n}x{n * world} (Ra=1e5 Da=1e-3 eps=0.4 Pr=1 Le=5 "
+                               f"N=-1, L = nx = {n}) cut into {world} slabs of {n} rows, "
+                               f"{args.precision} two-buffer pull, halo exchange every step "
+                               f"over {args.comm}",
+                   "parallelism": f"y-slabs x{world}", "wall_s": wall_s},
+        "halo_bytes_per_step_per_cut": 2 * nb,
+        "clocks": clk.summary(),
+        "nusselt_sherwood": [float(x) for x in nush], "residual": r,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    slab.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def l2_copy_gbs(stream, mb):
+    """Best-of-10 copy bandwidth (read + write bytes) of `mb` MB each way, back to back."""
+    import torch
+    n = mb * (1 << 20) // 4
+    a = torch.rand(n, device="cuda")
+    b = torch.empty_like(a)
+    reps = max(10, int(4e9 / (2 * n * 4)))
+    for _ in range(3):
+        b.copy_(a)
+    best = 0.0
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, 2 * n * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
+
+
+def run_l2peak(args):
+    """Copy bandwidth of a working set that stays in L2 (the bound of the batched step,
+    whose L2 blocking keeps a group's state in L2 for most of its steps): torch copies
+    b <- a of `--l2-mb` MB each way, repeated back to back, timed with CUDA events;
+    read + write bytes over time, best of 10 rounds, for several sizes."""
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {str(mb): l2_copy_gbs(stream, mb) for mb in [int(x) for x in args.l2_mb.split(",")]}
+    line = {"metric": "L2-resident copy bandwidth", "mode": "l2peak", "unit": "GB/s",
+            "value": max(out.values()), "by_mb_each_way": out,
+            "how": "torch copy_ of float32 buffers (read + write bytes), back to back, CUDA "
+                   "events, best of 10 rounds",
+            "l2_bytes": torch.cuda.get_device_properties(0).L2_cache_size}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch(args):
     """Many uneven cavities (grids drawn from 32^2..256^2, parameters drawn from the
     mixed ranges) advanced together: one fused launch per L2-sized group per step,
@@ -386,6 +551,12 @@ def run_batch(args):
     glups = nodes * args.batch_steps / (ms / 1e3) / 1e9
     nush = b.nusselt_sherwood()
     b.close()
+    # the roofline: L2 blocking keeps a group's state in L2 for all but the first of its
+    # steps, so the bound is the L2-resident copy bandwidth (measured here, 16 MB each way)
+    l2_peak = l2_copy_gbs(stream, 16)
+    hbm_peak, peak_kind = measured_peaks()
+    bpn = BYTES_PER_NODE[args.precision]
+    achieved = glups * bpn
     # one launch per cavity per step, on one stream
     cavs = [lbm.Cavity(*s.args(), varpi=s.varpi, precision=args.precision, layout=args.layout,
                        seed=s.seed, noise=s.noise, stream=stream.cuda_stream, graph_chunk=-1)
@@ -409,8 +580,15 @@ def run_batch(args):
         "data": "synthetic",
         "config": {"workload": f"{args.count} cavities, grids 32^2-256^2 drawn by seed 4, "
                                f"log-uniform Ra in [1e3,1e5], Da in [1e-4,1e-1], uniform eps, Le, N, "
-                               f"sigma; {args.precision} {args.layout}",
+                               f"sigma, varpi = min(0.4, 0.8 min(eps, sigma)); "
+                               f"{args.precision} {args.layout}",
                    "nodes": nodes, "time_steps": args.batch_steps},
+        "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
+                     "frac": achieved / l2_peak, "traffic": None,
+                     "peak_source": "L2-resident copy, 16 MB each way, measured in this run",
+                     "kernel": f"batch_step_kernel<{args.precision}>",
+                     "algorithmic_bytes_per_node": bpn,
+                     "frac_of_hbm": achieved / hbm_peak, "hbm_peak": hbm_peak},
         "one_launch_per_cavity_glups": per_glups,
         "speedup_vs_one_launch_per_cavity": glups / per_glups,
         "autotune_s": tune_s, "autotune": report.strip().splitlines(),
@@ -421,10 +599,54 @@ def run_batch(args):
     return 0
 
 
+def solve_alone(lbm, spec, precision, layout, stream, tol, nush_tol, check, cap):
+    """One cavity solve on its own (one fused launch per time step, CUDA graphs), stopped
+    by the server's rule: at a check every `check` steps it is steady if the residual
+    over those steps is below tol, or (from the second check on) if every Nu_L, Sh_L,
+    Nu_R, Sh_R moved by less than nush_tol relative since the previous check; past `cap`
+    steps it is unconverged; a non-finite value makes it diverged."""
+    import numpy as np
+    c = lbm.Cavity(*spec.args(), varpi=spec.varpi, precision=precision, layout=layout,
+                   seed=spec.seed, noise=spec.noise, stream=stream)
+    prev = np.zeros(4)
+    steps, checks, status, r, ns = 0, 0, 6, float("inf"), prev
+    while True:
+        c.step(check)
+        steps += check
+        checks += 1
+        try:
+            r = c.residual()
+            ns = c.nusselt_sherwood()
+        except lbm.LbmError:
+            status = 4
+            break
+        dn = float(np.max(np.abs(ns - prev) / np.maximum(np.abs(ns), 1e-300)))
+        prev = ns
+        if (tol > 0 and r < tol) or (nush_tol > 0 and checks > 1 and dn < nush_tol):
+            status = 0
+            break
+        if steps >= cap:
+            break
+    c.close()
+    return {"status": status, "steps": steps, "residual": r, "nush": list(map(float, ns))}
+
+
+def fifo_latency(arrive, service):
+    """Latencies of a one-at-a-time server (FIFO, one request on the device at a time)
+    for the given arrival times and measured service times."""
+    t, lat = 0.0, []
+    for a, s in zip(arrive, service):
+        t = max(t, a) + s
+        lat.append(t - a)
+    return lat
+
+
 def run_serve(args):
-    """Continuous-batching solver service against plain one-at-a-time FP64 solves.
-    Requests: grids from `--serve-sizes`, parameters from the mixed ranges, Poisson
-    arrivals at 0.8 x the service capacity measured on a burst of the same requests."""
+    """Continuous-batching solver service against one-at-a-time solves of the same
+    requests in the same storage precision and in plain FP64, all stopped by the same
+    rule.  Requests: grids from `--serve-sizes`, parameters from the mixed ranges (seed 5),
+    Poisson arrivals at 0.8 x the service capacity measured on a burst of the same
+    requests (or `--arrival-rate`)."""
     import numpy as np
     import torch
     from paper_1708_07525_gb300 import lbm
@@ -435,23 +657,19 @@ def run_serve(args):
     sizes = tuple(int(x) for x in args.serve_sizes.split(","))
     specs = draw_batch(args.requests, seed=5, sizes=sizes)
     insts = [lbm.make_instance(s) for s in specs]
-    cap_steps = args.max_steps
-    check = args.check_every
+    cap, check, tol, ntol = args.max_steps, args.check_every, args.serve_tol, args.nush_tol
 
     def serve(arrive):
         srv = lbm.Server(args.budget_gb * (1 << 30), max_slots=len(specs), check_every=check,
                          precision=args.precision, layout=args.layout, stream=stream.cuda_stream)
         t_start = time.perf_counter()
         pending = list(range(len(specs)))
-        submitted_at = {}
         done = {}
         while len(done) < len(specs):
             now = time.perf_counter() - t_start
             while pending and arrive[pending[0]] <= now:
                 k = pending.pop(0)
-                srv.submit(insts[k], tol=args.serve_tol, nush_tol=args.nush_tol,
-                           max_steps=cap_steps, rid=k)
-                submitted_at[k] = now
+                srv.submit(insts[k], tol=tol, nush_tol=ntol, max_steps=cap, rid=k)
             active = srv.tick()
             t_now = time.perf_counter() - t_start
             for r in srv.poll():
@@ -462,79 +680,174 @@ def run_serve(args):
         srv.close()
         return done, makespan
 
-    burst, burst_s = serve(np.zeros(len(specs)))
-    capacity = len(specs) / burst_s
-    arr = arrivals(len(specs), 0.8 * capacity, seed=5)
+    if args.arrival_rate > 0:
+        capacity = None
+        rate = args.arrival_rate
+    else:
+        _, burst_s = serve(np.zeros(len(specs)))
+        capacity = len(specs) / burst_s
+        rate = 0.8 * capacity
+    arr = arrivals(len(specs), rate, seed=5)
     arr = arr - arr[0]
     served, served_s = serve(arr)
     lat = np.array([served[k]["finished"] - served[k]["arrival"] for k in served])
 
-    # plain path: one FP64 cavity at a time, same check interval, residual < fp64_tol
-    plain = {}
-    plain_s = None
-    if args.plain_cache and os.path.exists(args.plain_cache):
-        with open(args.plain_cache) as f:
-            cached = json.load(f)
-        plain = {int(k): v for k, v in cached["plain"].items()}
-        plain_s = cached["seconds"]
-    t0 = time.perf_counter()
-    for k, s in enumerate(specs if plain_s is None else []):
-        if time.perf_counter() - t0 > args.plain_budget_s:
-            break
-        c = lbm.Cavity(*s.args(), varpi=s.varpi, precision="f64", seed=s.seed, noise=s.noise,
-                       stream=stream.cuda_stream)
-        status, steps = "unconverged", 0
-        c.residual()
-        while steps < cap_steps:
-            c.step(check)
-            steps += check
-            if c.residual() < args.fp64_tol:
-                status = "ok"
+    fp64_service = [None]
+
+    def alone(precision, budget_s):
+        res, service = {}, []
+        if precision == "f64":
+            fp64_service[0] = service
+        t0 = time.perf_counter()
+        for k, s in enumerate(specs):
+            if time.perf_counter() - t0 > budget_s:
                 break
-        plain[k] = {"nush": c.nusselt_sherwood().tolist(), "steps": steps, "status": status}
-        c.close()
-    if plain_s is None:
-        plain_s = time.perf_counter() - t0
-        if args.plain_cache:
-            with open(args.plain_cache, "w") as f:
-                json.dump({"plain": plain, "seconds": plain_s}, f)
-    errs = []
-    for k, p in plain.items():
-        if p["status"] == "ok" and served[k]["status"] == 0:
-            a, b = np.array(served[k]["nush"]), np.array(p["nush"])
-            errs.append(float(np.max(np.abs(a - b) / np.abs(b))))
-    errs = np.array(errs) if errs else np.array([np.nan])
-    statuses = [served[k]["status"] for k in served]
+            t1 = time.perf_counter()
+            res[k] = solve_alone(lbm, s, precision, "ab", stream.cuda_stream, tol, ntol, check,
+                                 cap)
+            torch.cuda.synchronize()
+            service.append(time.perf_counter() - t1)
+        secs = time.perf_counter() - t0
+        l = np.array(fifo_latency(arr[:len(service)], service)) if service else np.array([np.nan])
+        return res, secs, l
+
+    same, same_s, same_lat = alone(args.precision, args.plain_budget_s)
+    if args.fp64_cache and os.path.exists(args.fp64_cache):   # the FP64 arm of an earlier run
+        with open(args.fp64_cache) as f:
+            cached = json.load(f)
+        fp64 = {int(k): v for k, v in cached["results"].items()}
+        fp64_s = cached["seconds"]
+        fp64_lat = np.array(fifo_latency(arr[:len(fp64)], cached["service"]))
+    else:
+        fp64, fp64_s, fp64_lat = alone("f64", args.plain_budget_s)
+        if args.fp64_cache:
+            with open(args.fp64_cache, "w") as f:
+                json.dump({"results": fp64, "seconds": fp64_s, "service": fp64_service[0]}, f)
+
+    def errs_vs(ref, other):
+        e = []
+        for k, p in ref.items():
+            if k in other and p["status"] == 0 and other[k]["status"] == 0:
+                a, b = np.array(other[k]["nush"]), np.array(p["nush"])
+                e.append(float(np.max(np.abs(a - b) / np.abs(b))))
+        return np.array(e) if e else np.array([np.nan])
+
+    def status_counts(res):
+        st = [r["status"] for r in res.values()]
+        return {"ok": st.count(0), "unconverged": st.count(6), "diverged": st.count(4)}
+
+    def pct(a, q):
+        return float(np.nanpercentile(a, q)) if np.isfinite(a).any() else None
+
+    e_served = errs_vs(fp64, served)
+    e_same = errs_vs(fp64, same)
+    nodes = {k: s.nx * s.ny for k, s in enumerate(specs)}
     line = {
         "metric": METRIC, "mode": "serve", "value": len(specs) / served_s, "unit": "solves/s",
         "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": f"{len(specs)} cavity solve requests, grids {sizes}, parameters "
-                               f"from the mixed ranges (seed 5), Poisson arrivals at 0.8 x burst "
-                               f"capacity; steady when residual < {args.serve_tol} or Nu/Sh change "
-                               f"< {args.nush_tol} per {check} steps; cap {cap_steps} steps",
-                   "precision": args.precision, "budget_gb": args.budget_gb},
+        "config": {"workload": f"first {len(specs)} of the seeded cavity solve requests (seed 5), "
+                               f"grids {sizes}, parameters from the mixed ranges with varpi = "
+                               f"min(0.4, 0.8 min(eps, sigma)), Poisson arrivals at "
+                               f"{rate:.3g}/s; every arm stops a request at the first check "
+                               f"(every {check} steps) where the residual < {tol} or every "
+                               f"Nu/Sh moved < {ntol} relative, else at {cap} steps",
+                   "precision": args.precision, "layout": args.layout,
+                   "budget_gb": args.budget_gb,
+                   "grids": {str(n): sum(1 for s in specs if s.nx == n) for n in sizes},
+                   "lattice_updates": int(sum(nodes[k] * served[k]["steps"] for k in served))},
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "max": float(lat.max())},
         "burst_capacity_solves_per_s": capacity,
-        "served_status": {"ok": statuses.count(0), "unconverged": statuses.count(6),
-                          "diverged": statuses.count(4)},
-        "plain_fp64": {"solves": len(plain), "solves_per_s": len(plain) / plain_s,
-                       "converged": sum(p["status"] == "ok" for p in plain.values()),
-                       "tol": args.fp64_tol},
-        "speedup_vs_plain_fp64": (len(specs) / served_s) / (len(plain) / plain_s),
-        "nush_rel_err_vs_fp64": {"n": int(np.isfinite(errs).sum()),
-                                 "max": float(np.nanmax(errs)), "median": float(np.nanmedian(errs)),
-                                 "frac_le_1e-3": float(np.mean(errs <= 1e-3))},
+        "served_status": status_counts(served),
+        "one_at_a_time": {
+            "precision": args.precision, "solves": len(same), "seconds": same_s,
+            "solves_per_s": len(same) / same_s, "status": status_counts(same),
+            "latency_s": {"p50": pct(same_lat, 50), "p99": pct(same_lat, 99)},
+            "nush_rel_err_vs_fp64": {"n": int(np.isfinite(e_same).sum()),
+                                     "max": float(np.nanmax(e_same)) if np.isfinite(e_same).any() else None}},
+        "plain_fp64": {
+            "solves": len(fp64), "seconds": fp64_s, "solves_per_s": len(fp64) / fp64_s,
+            "status": status_counts(fp64),
+            "latency_s": {"p50": pct(fp64_lat, 50), "p99": pct(fp64_lat, 99)}},
+        "speedup_vs_one_at_a_time": (len(specs) / served_s) / (len(same) / same_s)
+                                    if len(same) == len(specs) else None,
+        "speedup_vs_plain_fp64": (len(specs) / served_s) / (len(fp64) / fp64_s),
+        "nush_rel_err_vs_fp64": {"n": int(np.isfinite(e_served).sum()),
+                                 "max": float(np.nanmax(e_served)) if np.isfinite(e_served).any() else None,
+                                 "median": float(np.nanmedian(e_served)) if np.isfinite(e_served).any() else None,
+                                 "frac_le_1e-3": float(np.mean(e_served <= 1e-3))},
+        "steps": {str(k): served[k]["steps"] for k in sorted(served)},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve_cost(args):
+    """Total lattice updates of the seeded request stream (`--requests-total` requests,
+    seed 5, grids from `--serve-sizes`) under the serving stop rule.  Every request's
+    parameters are solved at 64^2 in the server (storage `--precision`); the steps to
+    the stop rule scale with the grid width (the mapping of Sec. 4.1 fixes U and makes
+    nu, alpha_e, D_e grow with L, so every time scale in steps grows like L), so a
+    request on an L^2 grid is estimated at steps_64 * L / 64 steps of L^2 nodes."""
+    import numpy as np
+    import torch
+    from dataclasses import replace
+    from paper_1708_07525_gb300 import lbm
+    from paper_1708_07525_gb300.workloads import draw_batch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sizes = tuple(int(x) for x in args.serve_sizes.split(","))
+    specs = draw_batch(args.requests_total, seed=5, sizes=sizes)
+    small = [lbm.make_instance(replace(s, nx=64, ny=64)) for s in specs]
+    cap64 = args.max_steps
+    srv = lbm.Server(args.budget_gb * (1 << 30), max_slots=len(specs),
+                     check_every=args.check_every, precision=args.precision,
+                     stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    for k, inst in enumerate(small):
+        srv.submit(inst, tol=args.serve_tol, nush_tol=args.nush_tol, max_steps=cap64, rid=k)
+    res = {r["id"]: r for r in srv.drain()}
+    secs = time.perf_counter() - t0
+    srv.close()
+    steps64 = np.array([res[k]["steps"] for k in range(len(specs))], dtype=float)
+    status = np.array([res[k]["status"] for k in range(len(specs))])
+    L = np.array([s.nx for s in specs], dtype=float)
+    steps = steps64 * L / 64.0
+    updates = steps * L * L
+    cum = np.cumsum(updates)
+    prefixes = {str(n): float(cum[n - 1]) for n in (8, 16, 24, 32, 64, 128, 256, 512, 1000,
+                                                    2000) if n <= len(specs)}
+    line = {
+        "metric": METRIC, "mode": "serve_cost", "value": float(updates.sum()), "unit": "lattice updates",
+        "data": "synthetic", "dtype": args.precision,
+        "config": {"workload": f"{len(specs)} seeded cavity solve requests (seed 5), grids {sizes}; "
+                               f"stop rule: residual < {args.serve_tol} or Nu/Sh change < "
+                               f"{args.nush_tol} per {args.check_every} steps; each request "
+                               f"solved at 64^2 (cap {cap64} steps), steps scaled by L / 64"},
+        "calibration_seconds": secs,
+        "calibration_status_64": {"ok": int((status == 0).sum()), "unconverged": int((status == 6).sum()),
+                                  "diverged": int((status == 4).sum())},
+        "steps_64": {"p50": float(np.median(steps64)), "p90": float(np.percentile(steps64, 90)),
+                     "max": float(steps64.max())},
+        "updates_by_grid": {str(int(n)): float(updates[L == n].sum()) for n in sizes},
+        "count_by_grid": {str(int(n)): int((L == n).sum()) for n in sizes},
+        "cumulative_updates_of_prefix": prefixes,
+        "hours_at_40_glups": float(updates.sum() / 40e9 / 3600),
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
 def run_precision(args):
-    """Storage-precision study on the 1024^2 cavity (Ra 1e5, Da 1e-2, eps 0.6, Le 10,
-    N 2): FP64 (reference), FP32, and shifted FP16 / BF16 with stochastic rounding,
-    all FP32 arithmetic but FP64; the same number of steps; errors of u, T, C
-    (relative L2) and of Nu/Sh against FP64; FP64 reductions throughout."""
+    """Storage-precision study on the 1024^2 cavity (Ra 1e5, Da 1e-2, eps 0.6, Le 10, N 2)
+    against a steady FP64 state.  FP32 storage runs `--prec-steps` steps to its rounding
+    floor; its state is loaded into an FP64 context (exact widening of every stored
+    deviation) and run on in FP64 until the relative change of u, T, C over
+    `--prec-check` steps is below `--steady-tol` (the reference, steady in FP64).  FP16 and
+    BF16 storage (FP32 arithmetic, stochastic rounding) run `--prec-steps` steps from t = 0.
+    Every result is compared with the reference: relative L2 error of u, T, C and the
+    largest relative error of Nu_L, Sh_L, Nu_R, Sh_R (Eq. 38); reductions in FP64."""
     import numpy as np
     import torch
     from paper_1708_07525_gb300 import lbm
@@ -543,40 +856,67 @@ def run_precision(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     steps, check = args.prec_steps, args.prec_check
-    out = {}
-    ref = None
-    for prec in args.prec_list.split(","):
-        c = lbm.Cavity(*spec.args(), precision=prec, seed=spec.seed, noise=spec.noise,
-                       stream=stream.cuda_stream)
+
+    def run(c, until, stop_tol=0.0):
         c.residual()
-        hist = []
+        hist, ms = [], 0.0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ms = 0.0
-        while c.t < steps:
+        t_begin = c.t
+        while c.t < until:
             e0.record(stream)
-            c.step(min(check, steps - c.t))
+            c.step(min(check, until - c.t))
             e1.record(stream)
             r = c.residual()
             ms += e0.elapsed_time(e1)
             hist.append([c.t, r] + c.nusselt_sherwood().tolist())
+            if stop_tol > 0 and r < stop_tol:
+                break
+        glups = spec.nx * spec.ny * (c.t - t_begin) / (ms / 1e3) / 1e9
+        return hist, glups
+
+    def make(prec):
+        return lbm.Cavity(*spec.args(), precision=prec, seed=spec.seed, noise=spec.noise,
+                          stream=stream.cuda_stream)
+
+    out = {}
+    c32 = make("f32")
+    hist32, g32 = run(c32, steps)
+    f32 = c32.fields(("ux", "uy", "T", "C"))
+    blob = c32.save()
+    c32.close()
+    c64 = make("f64")
+    c64.load(blob)
+    hist64, g64 = run(c64, steps + args.polish_cap, stop_tol=args.steady_tol)
+    ref = (c64.fields(("ux", "uy", "T", "C")), np.array(hist64[-1][2:]))
+    c64.close()
+    out["f64"] = {"glups": g64, "start": f"the FP32 state at {steps} steps", "steps": hist64[-1][0],
+                  "final_residual": hist64[-1][1], "steady": hist64[-1][1] < args.steady_tol,
+                  "nush": hist64[-1][2:]}
+
+    def compare(fl, nush):
+        return ({k: float(np.linalg.norm(fl[k] - ref[0][k]) / np.linalg.norm(ref[0][k])) for k in fl},
+                float(np.max(np.abs(np.array(nush) - ref[1]) / np.abs(ref[1]))))
+
+    e, en = compare(f32, hist32[-1][2:])
+    out["f32"] = {"glups": g32, "steps": steps, "final_residual": hist32[-1][1],
+                  "nush": hist32[-1][2:], "rel_l2_err": e, "nush_rel_err": en}
+    for prec in [p for p in args.prec_list.split(",") if p in ("bf16", "f16")]:
+        c = make(prec)
+        hist, g = run(c, steps)
         fl = c.fields(("ux", "uy", "T", "C"))
-        rec = {"glups": spec.nx * spec.ny * steps / (ms / 1e3) / 1e9, "final_residual": hist[-1][1],
-               "nush": hist[-1][2:], "history": hist}
-        if ref is None:
-            ref = (fl, np.array(hist[-1][2:]))
-        else:
-            rec["rel_l2_err"] = {k: float(np.linalg.norm(fl[k] - ref[0][k]) / np.linalg.norm(ref[0][k]))
-                                 for k in fl}
-            rec["nush_rel_err"] = float(np.max(np.abs(np.array(hist[-1][2:]) - ref[1]) / np.abs(ref[1])))
-        out[prec] = rec
         c.close()
+        e, en = compare(fl, hist[-1][2:])
+        out[prec] = {"glups": g, "steps": steps, "final_residual": hist[-1][1], "nush": hist[-1][2:],
+                     "rel_l2_err": e, "nush_rel_err": en}
         if args.partial_out:   # results so far, in case a long study is cut short
             with open(args.partial_out, "w") as f:
                 json.dump(out, f)
     line = {"metric": METRIC, "mode": "precision", "unit": "relative error", "data": "synthetic",
             "config": {"workload": f"{spec.nx}x{spec.ny} cavity Ra={spec.Ra} Da={spec.Da} eps={spec.eps} "
-                                   f"Le={spec.Le} N={spec.N}", "steps": steps, "check_every": check},
-            "results": {k: {kk: vv for kk, vv in v.items() if kk != "history"} for k, v in out.items()}}
+                                   f"Le={spec.Le} N={spec.N}", "steps": steps, "check_every": check,
+                       "reference": f"FP64 from the FP32 state at {steps} steps until the relative "
+                                    f"change over {check} steps < {args.steady_tol}"},
+            "results": out}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -597,34 +937,51 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=1)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "precision"])
-    ap.add_argument("--prec-steps", type=int, default=2500000)
+    ap.add_argument("--split", default="replicas", choices=["replicas", "slab"],
+                    help="N > 1: independent cavities per rank, or one cavity cut into y-slabs")
+    ap.add_argument("--comm", default="nccl", choices=["nccl", "gloo"],
+                    help="slab exchange: NCCL send/recv, or host-staged over gloo")
+    ap.add_argument("--device", type=int, default=0, help="--comm gloo: the GPU every rank uses")
+    ap.add_argument("--mode", default="step",
+                    choices=["step", "batch", "serve", "serve_cost", "precision", "l2peak"])
+    ap.add_argument("--l2-mb", default="4,8,16,24,32,48")
+    ap.add_argument("--prec-steps", type=int, default=4000000)
     ap.add_argument("--prec-check", type=int, default=100000)
-    ap.add_argument("--prec-list", default="f64,f32,f16,bf16")
+    ap.add_argument("--prec-list", default="f32,f16,bf16")
+    ap.add_argument("--steady-tol", type=float, default=1e-8)
+    ap.add_argument("--polish-cap", type=int, default=3000000)
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--requests", type=int, default=32)
-    ap.add_argument("--serve-sizes", default="64,128")
-    ap.add_argument("--serve-tol", type=float, default=1e-6)
-    ap.add_argument("--nush-tol", type=float, default=0.0)
-    ap.add_argument("--fp64-tol", type=float, default=1e-7)
+    ap.add_argument("--requests-total", type=int, default=2000)
+    ap.add_argument("--arrival-rate", type=float, default=0.0)
+    ap.add_argument("--serve-sizes", default="64,128,256,512,1024")
+    ap.add_argument("--serve-tol", type=float, default=1e-7)
+    ap.add_argument("--nush-tol", type=float, default=1e-7)
     ap.add_argument("--check-every", type=int, default=500)
     ap.add_argument("--max-steps", type=int, default=300000)
     ap.add_argument("--budget-gb", type=float, default=8.0)
     ap.add_argument("--plain-budget-s", type=float, default=120.0)
-    ap.add_argument("--plain-cache", default="")
     ap.add_argument("--partial-out", default="")
+    ap.add_argument("--fp64-cache", default="",
+                    help="serve: file holding the FP64 one-at-a-time arm (written if absent)")
     args = ap.parse_args()
     if args.mode == "batch":
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "serve_cost":
+        return run_serve_cost(args)
+    if args.mode == "l2peak":
+        return run_l2peak(args)
     if args.mode == "precision":
         return run_precision(args)
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.split == "slab":
+        return run_slab(args)
     return run_ours(args)
 
 

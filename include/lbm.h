@@ -261,6 +261,15 @@ lbm_status lbm_nusselt_sherwood_tb(lbm_ctx* ctx, double out[4]);
  * LBM_ERR_DIVERGED if a field value is not finite. */
 lbm_status lbm_residual(lbm_ctx* ctx, double* r);
 
+/* The maxima behind lbm_residual(), for combining several contexts (the slabs of
+ * one cavity): parts[q] = max |phi_now - phi_snap| and parts[4 + q] = max |phi_now|
+ * for phi = u_x, u_y, T, C (q = 0..3) over this context's rows; parts[0..3] = +inf
+ * on the first call.  The residual of the whole cavity is
+ * max over q of (max over slabs of parts[q]) / (max over slabs of parts[4 + q]).
+ * Replaces the snapshot as lbm_residual() does.  Synchronises the stream.
+ * LBM_ERR_DIVERGED if a field value is not finite. */
+lbm_status lbm_residual_parts(lbm_ctx* ctx, double parts[8]);
+
 /* Checkpoint of the full state (distributions, history, time, parameters).
  * lbm_save with buf == NULL stores the size needed in *len.  lbm_load
  * requires a checkpoint of a context with the same grid and layout; a
@@ -271,6 +280,45 @@ lbm_status lbm_residual(lbm_ctx* ctx, double* r);
  * when narrowing).  Both synchronise the stream. */
 lbm_status lbm_save(lbm_ctx* ctx, void* buf, size_t* len);
 lbm_status lbm_load(lbm_ctx* ctx, const void* buf, size_t len);
+
+/* ---- A cavity split along y into slabs ---------------------------------------
+ * One cavity of params->nx x params->ny nodes may be cut into slabs of whole rows,
+ * e.g. one per GPU.  Streaming (Eq. 11) pulls the populations with e_y = +1
+ * (f2, f5, f6, g2, h2) across a cut from the row below it and those with e_y = -1
+ * (f4, f7, f8, g4, h4) from the row above, so after every time step each slab sends
+ * those five values per column of its outermost rows to its neighbours, which
+ * store them in a ghost row beside the cut; the collision and everything else is
+ * local to a node.  With those exchanges after every step the slabs reproduce the
+ * undivided cavity's run bit for bit.  Slabs take halfway walls, the two-buffer
+ * layout and a uniform porous medium; any storage precision.
+ *
+ * lbm_create_slab: the slab of rows [y0, y0 + h) of the cavity described by params
+ * (the whole cavity's constants, e.g. from lbm_derive_params(); walls only where the
+ * slab meets the cavity's walls).  The initial noise takes the values those rows have
+ * in the whole cavity; T_init / C_init of opt are [h][nx].  Row j of lbm_fields(),
+ * lbm_fields_window() is the cavity's row y0 + j; lbm_nusselt_sherwood() gives the
+ * means over the slab's rows (the cavity's mean is the h-weighted mean over slabs);
+ * lbm_nusselt_sherwood_tb() is not defined on a slab (LBM_ERR_INVALID); for the
+ * residual of the whole cavity combine lbm_residual_parts() of all slabs.
+ * LBM_ERR_INVALID for rows outside the cavity, walls with nodes on them, the in-place
+ * layout or porous fields. */
+lbm_status lbm_create_slab(const lbm_params* params, int y0, int h, const lbm_options* opt,
+                           lbm_ctx** out);
+
+/* Bytes of one face: the five crossing populations of each of the nx columns, in the
+ * storage precision (5 * nx * element size), laid out [5][nx]. */
+lbm_status lbm_halo_bytes(const lbm_ctx* ctx, size_t* bytes);
+
+/* side 0: the cut below the slab, 1: the cut above it.  lbm_halo_export copies the
+ * populations of the slab's outermost row on that side that cross the cut (the
+ * post-collision values of the last step) into the caller-owned device buffer face;
+ * lbm_halo_import copies the neighbour's face (its export toward this slab) into the
+ * ghost row on that side.  Both are asynchronous on the context's stream (order them
+ * after the neighbour's export with events, or synchronise).  Call them between steps:
+ * after lbm_step(ctx, 1) on every slab, export on every slab, then import on every slab.
+ * LBM_ERR_INVALID if that side of the slab is a wall of the cavity. */
+lbm_status lbm_halo_export(lbm_ctx* ctx, int side, void* face);
+lbm_status lbm_halo_import(lbm_ctx* ctx, int side, const void* face);
 
 /* Parameters in use, and bytes of device memory the context holds. */
 lbm_status lbm_get_params(const lbm_ctx* ctx, lbm_params* out);

@@ -178,6 +178,8 @@ struct lbm_ctx {
     cudaStream_t aux = nullptr;           // second stream for the ring launches of split steps
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
+    int slab_y0 = 0;                // global row of the first updated row (0 for a cavity)
+    bool slab = false;              // a slab of a cavity split along y (lbm_create_slab)
     Coef<double> cd{};
     Coef<float> cf{};
     Coef<f2> cp{};                  // 16-bit storage: cf as pairs (two nodes per thread)
@@ -293,11 +295,14 @@ lbm_status do_init(lbm_ctx* c, const double* T_host, const double* C_host, uint6
     I.eps = c->P.eps;
     I.varpi = c->P.varpi;
     I.model_a = c->P.model_a;
-    const size_t n = c->nodes();
+    // noise keys of the whole cavity: a slab draws the values its rows have in it
+    I.key_ny = c->P.ny;
+    I.key_j0 = c->slab_y0 - c->G.jb;
+    const size_t n = (size_t)c->G.nx * step_rows(c->G);
     cudaError_t e = cudaSuccess;
     if (T_host) {
         if (!c->d_stage) {
-            c->d_stage = (double*)c->dalloc(2 * n * sizeof(double));
+            c->d_stage = (double*)c->dalloc(2 * c->nodes() * sizeof(double));
             if (!c->d_stage) return c->fail(LBM_ERR_NOMEM, "no device memory for initial fields");
         }
         e = cudaMemcpyAsync(c->d_stage, T_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
@@ -517,7 +522,11 @@ lbm_status lbm_params_model_a(lbm_params* p) {
     return LBM_OK;
 }
 
-lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_ctx** out) {
+namespace {
+
+// A cavity (slab_h = 0), or the slab of rows [slab_y0, slab_y0 + slab_h) of it.
+lbm_status create_core(const lbm_params* params, const lbm_options* opt, int slab_y0, int slab_h,
+                       lbm_ctx** out) {
     if (!params || !out) {
         set_global_error("lbm_create_raw: params and out must be non-NULL");
         return LBM_ERR_INVALID;
@@ -527,6 +536,19 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
     if (bad) {
         set_global_error("lbm_create_raw: %s", bad);
         return LBM_ERR_INVALID;
+    }
+    const bool slab = slab_h > 0;
+    if (slab) {
+        if (slab_y0 < 0 || slab_y0 + slab_h > params->ny) {
+            set_global_error("lbm_create_slab: rows [%d, %d) outside the %d rows of the cavity",
+                             slab_y0, slab_y0 + slab_h, params->ny);
+            return LBM_ERR_INVALID;
+        }
+        if (params->nee || (opt && (opt->layout != LBM_AB_PULL || opt->eps_field || opt->K_field))) {
+            set_global_error("lbm_create_slab: slabs take halfway walls, the two-buffer layout "
+                             "and a uniform porous medium");
+            return LBM_ERR_INVALID;
+        }
     }
     lbm_options O;
     std::memset(&O, 0, sizeof O);
@@ -577,10 +599,19 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
         }
         c->own_stream = true;
     }
-    const int nx = params->nx, ny = params->ny;
+    const int nx = params->nx;
+    // a slab holds a ghost row beside each side that is a cut rather than a wall
+    const int glo = slab && slab_y0 > 0 ? 1 : 0;
+    const int ghi = slab && slab_y0 + slab_h < params->ny ? 1 : 0;
+    const int rows = slab ? slab_h : params->ny;
+    const int ny = rows + glo + ghi;
     const int per128 = (int)(128 / c->esz);
+    c->slab = slab;
+    c->slab_y0 = slab ? slab_y0 : 0;
     c->G.nx = nx;
     c->G.ny = ny;
+    c->G.jb = glo;
+    c->G.je = glo + rows;
     c->G.pitch = (nx + per128 - 1) / per128 * per128;
     c->G.plane = (size_t)ny * c->G.pitch;
     c->cd = make_coef<double>(c->P);
@@ -589,6 +620,8 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
     c->cf.sr = c->round_nearest ? 0 : 1;
     c->cp = make_coef<f2>(c->P);
     c->cp.sr = c->cf.sr;
+    // rounding streams keyed by the node's index in the undivided cavity
+    c->cf.seed_off = (long long)(c->slab_y0 - c->G.jb) * c->G.pitch;
     int bx = O.block_x, by = O.block_y;
     if (bx == 0) bx = nx >= 128 ? 128 : 32;
     if (by == 0) by = bx >= 128 ? 1 : 128 / bx;
@@ -603,7 +636,9 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
     c->L.by = by;
     c->L.stream = c->stream;
     c->L.aux = nullptr;
-    c->L.pair = (c->prec == LBM_BF16 || c->prec == LBM_F16) ? &c->cp : nullptr;
+    // 16-bit storage takes the two-nodes-per-thread kernels, except on slabs, whose rows
+    // all run the one-node kernel (the same arithmetic as a one-node whole cavity)
+    c->L.pair = (c->prec == LBM_BF16 || c->prec == LBM_F16) && !slab ? &c->cp : nullptr;
     // a second stream lets the small ring launch of a split step run beside the inner one;
     // without it both go to the context's stream
     if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) == cudaSuccess &&
@@ -705,6 +740,21 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
     return LBM_OK;
 }
 
+}  // namespace
+
+lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_ctx** out) {
+    return create_core(params, opt, 0, 0, out);
+}
+
+lbm_status lbm_create_slab(const lbm_params* params, int y0, int h, const lbm_options* opt,
+                           lbm_ctx** out) {
+    if (h < 1) {
+        set_global_error("lbm_create_slab: a slab needs at least one row");
+        return LBM_ERR_INVALID;
+    }
+    return create_core(params, opt, y0, h, out);
+}
+
 lbm_status lbm_create(lbm_grid grid, double Ra, double Da, double eps, double Pr, double Le,
                       double N, double J, double sigma, const lbm_options* opt, lbm_ctx** out) {
     lbm_params P;
@@ -779,9 +829,11 @@ lbm_status lbm_fields_window(lbm_ctx* c, int x0, int y0, int w, int h, double* u
         set_global_error("lbm_fields_window: NULL context");
         return LBM_ERR_INVALID;
     }
-    if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || x0 + w > c->G.nx || y0 + h > c->G.ny || h > 65535)
+    const int rows = step_rows(c->G);
+    if (x0 < 0 || y0 < 0 || w < 1 || h < 1 || x0 + w > c->G.nx || y0 + h > rows || h > 65535)
         return c->fail(LBM_ERR_INVALID, "lbm_fields_window: window (%d, %d, %d x %d) outside the %d x %d grid",
-                       x0, y0, w, h, c->G.nx, c->G.ny);
+                       x0, y0, w, h, c->G.nx, rows);
+    y0 += c->G.jb;   // a slab's rows start after its lower ghost row
     DeviceGuard dg(c->device);
     const size_t n = (size_t)w * h;
     if (n > c->fields_cap) {
@@ -814,9 +866,10 @@ lbm_status lbm_fields(lbm_ctx* c, double* ux, double* uy, double* T, double* C, 
     }
     // whole grid, in row bands of at most 65535 rows and about 2^26 nodes (2.7 GB of read-out)
     const int band = (int)std::max<size_t>(1, std::min<size_t>(65535, ((size_t)1 << 26) / c->G.nx));
-    if (c->G.ny <= band) return lbm_fields_window(c, 0, 0, c->G.nx, c->G.ny, ux, uy, T, C, rho);
-    for (int y0 = 0; y0 < c->G.ny; y0 += band) {
-        const int h = std::min(band, c->G.ny - y0);
+    const int rows = step_rows(c->G);
+    if (rows <= band) return lbm_fields_window(c, 0, 0, c->G.nx, rows, ux, uy, T, C, rho);
+    for (int y0 = 0; y0 < rows; y0 += band) {
+        const int h = std::min(band, rows - y0);
         const size_t off = (size_t)y0 * c->G.nx;
         lbm_status s = lbm_fields_window(c, 0, y0, c->G.nx, h, ux ? ux + off : nullptr, uy ? uy + off : nullptr,
                                          T ? T + off : nullptr, C ? C + off : nullptr, rho ? rho + off : nullptr);
@@ -864,6 +917,7 @@ lbm_status lbm_nusselt_sherwood_tb(lbm_ctx* c, double out[4]) {
         set_global_error("lbm_nusselt_sherwood_tb: NULL argument");
         return LBM_ERR_INVALID;
     }
+    if (c->slab) return c->fail(LBM_ERR_INVALID, "lbm_nusselt_sherwood_tb: not defined on a slab");
     DeviceGuard dg(c->device);
     WallSpec W;
     W.Tw[0] = c->P.Tw[2];
@@ -892,17 +946,18 @@ lbm_status lbm_nusselt_sherwood_tb(lbm_ctx* c, double out[4]) {
     return LBM_OK;
 }
 
-lbm_status lbm_residual(lbm_ctx* c, double* r) {
-    if (!c || !r) {
-        set_global_error("lbm_residual: NULL argument");
-        return LBM_ERR_INVALID;
-    }
+namespace {
+
+// The residual pass over the updated rows: h[0..3] = max |phi_now - phi_snap|,
+// h[4..7] = max |phi_now| (phi = u_x, u_y, T, C), h[8] != 0 if a value is not finite;
+// the snapshot is replaced by phi_now.
+lbm_status residual_maxima(lbm_ctx* c, const char* who, double h[9]) {
     DeviceGuard dg(c->device);
     const size_t n = c->nodes();
     if (!c->d_snap) {
         c->d_snap = c->dalloc(4 * n * c->rsz);
         c->d_partial = (double*)c->dalloc((size_t)RES_SLOTS * 9 * sizeof(double));
-        if (!c->d_snap || !c->d_partial) return c->fail(LBM_ERR_NOMEM, "lbm_residual: no device memory");
+        if (!c->d_snap || !c->d_partial) return c->fail(LBM_ERR_NOMEM, "%s: no device memory", who);
     }
     const int mode = c->read_mode();
     const void* b = cur_buf(c);
@@ -912,20 +967,93 @@ lbm_status lbm_residual(lbm_ctx* c, double* r) {
         launch_residual<float>(b, c->G, c->cf, mode, c->d_snap, c->d_partial, o, c->stream),
         launch_residual<__nv_bfloat16>(b, c->G, c->cf, mode, c->d_snap, c->d_partial, o, c->stream),
         launch_residual<__half>(b, c->G, c->cf, mode, c->d_snap, c->d_partial, o, c->stream));
-    double h[9];
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h, o, 9 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return c->cuda_fail(e, "lbm_residual");
-    if (h[8] != 0.0) return c->fail(LBM_ERR_DIVERGED, "lbm_residual: non-finite field at t=%lld", (long long)c->t);
+    if (e != cudaSuccess) return c->cuda_fail(e, who);
+    if (h[8] != 0.0) return c->fail(LBM_ERR_DIVERGED, "%s: non-finite field at t=%lld", who, (long long)c->t);
+    if (!c->snap_valid)   // no earlier fields: the changes are unknown
+        for (int q = 0; q < 4; ++q) h[q] = INFINITY;
+    c->snap_valid = true;
+    return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_residual(lbm_ctx* c, double* r) {
+    if (!c || !r) {
+        set_global_error("lbm_residual: NULL argument");
+        return LBM_ERR_INVALID;
+    }
+    double h[9];
+    lbm_status st = residual_maxima(c, "lbm_residual", h);
+    if (st != LBM_OK) return st;
     double res = 0.0;
     for (int q = 0; q < 4; ++q) {
         double rq = h[4 + q] > 0 ? h[q] / h[4 + q] : (h[q] > 0 ? INFINITY : 0.0);
         res = rq > res ? rq : res;
     }
-    *r = c->snap_valid ? res : INFINITY;
-    c->snap_valid = true;
+    *r = res;
     return LBM_OK;
+}
+
+lbm_status lbm_residual_parts(lbm_ctx* c, double parts[8]) {
+    if (!c || !parts) {
+        set_global_error("lbm_residual_parts: NULL argument");
+        return LBM_ERR_INVALID;
+    }
+    double h[9];
+    lbm_status st = residual_maxima(c, "lbm_residual_parts", h);
+    if (st != LBM_OK) return st;
+    for (int q = 0; q < 8; ++q) parts[q] = h[q];
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_bytes(const lbm_ctx* c, size_t* bytes) {
+    if (!c || !bytes) {
+        set_global_error("lbm_halo_bytes: NULL argument");
+        return LBM_ERR_INVALID;
+    }
+    *bytes = 5 * (size_t)c->G.nx * c->esz;
+    return LBM_OK;
+}
+
+namespace {
+
+// side 0: the cut below the slab, 1: the cut above it.  Export reads the populations of
+// the slab's outermost updated row that cross the cut; import writes the neighbour's into
+// the ghost row on that side.
+lbm_status halo_copy(lbm_ctx* c, int side, void* face, bool pack, const char* who) {
+    if (!c || !face || (side != 0 && side != 1)) {
+        set_global_error("%s: NULL argument or side not 0 / 1", who);
+        return LBM_ERR_INVALID;
+    }
+    const bool cut = side == 0 ? c->G.jb > 0 : c->G.je < c->G.ny;
+    if (!cut) return c->fail(LBM_ERR_INVALID, "%s: side %d of this context is a wall, not a cut", who, side);
+    DeviceGuard dg(c->device);
+    // export below: the bottom row's downward populations; export above: the top row's
+    // upward ones; import below fills the lower ghost row with the upward populations of
+    // the slab beneath, import above the upper ghost row with the downward ones
+    const int row = pack ? (side == 0 ? c->G.jb : c->G.je - 1) : (side == 0 ? c->G.jb - 1 : c->G.je);
+    const int up = pack ? side : 1 - side;
+    void* b = c->layout == LBM_AB_PULL ? c->buf[c->cur] : c->buf[0];
+    const int pk = pack ? 1 : 0;
+    cudaError_t e = LBM_DISPATCH(c, launch_halo<double>(b, c->G, row, up, face, pk, c->stream),
+                                 launch_halo<float>(b, c->G, row, up, face, pk, c->stream),
+                                 launch_halo<__nv_bfloat16>(b, c->G, row, up, face, pk, c->stream),
+                                 launch_halo<__half>(b, c->G, row, up, face, pk, c->stream));
+    if (e != cudaSuccess) return c->cuda_fail(e, who);
+    return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_halo_export(lbm_ctx* c, int side, void* face) {
+    return halo_copy(c, side, face, true, "lbm_halo_export");
+}
+
+lbm_status lbm_halo_import(lbm_ctx* c, int side, const void* face) {
+    return halo_copy(c, side, const_cast<void*>(face), false, "lbm_halo_import");
 }
 
 // Checkpoint layout: header, then the 19 state planes, then the 4 history planes.
@@ -1070,6 +1198,7 @@ lbm_status lbm_load(lbm_ctx* c, const void* buf, size_t len) {
     c->cf.sr = c->round_nearest ? 0 : 1;
     c->cp = make_coef<f2>(c->P);
     c->cp.sr = c->cf.sr;
+    c->cf.seed_off = (long long)(c->slab_y0 - c->G.jb) * c->G.pitch;
     c->cd.poro = (c->poro && c->rsz == 8) ? (const double*)c->poro : nullptr;
     c->cf.poro = (c->poro && c->rsz == 4) ? (const float*)c->poro : nullptr;
     if (c->graph) {   // constants are baked into the captured launches

@@ -45,6 +45,8 @@ Geom geom_for(int nx, int ny, int prec) {
     G.ny = ny;
     G.pitch = (nx + per128 - 1) / per128 * per128;
     G.plane = (size_t)ny * G.pitch;
+    G.jb = 0;
+    G.je = ny;
     return G;
 }
 
@@ -457,6 +459,8 @@ lbm_status init_slot(lbm_batch* b, int k) {
     I.eps = s.P.eps;
     I.varpi = s.P.varpi;
     I.model_a = s.P.model_a;
+    I.key_ny = s.G.ny;
+    I.key_j0 = 0;
     const Coef<float> c = coef_from(s.P, b->sr);
     const bool pull = b->layout == LBM_AB_PULL;
     void* buf0 = b->slot_buf(s, 0);

@@ -246,6 +246,10 @@ struct Coef {
     // equilibria as g_eq,0 = a0 Phi, g_eq,i = a1 Phi + (e_i . u) Phi / 2 (i = 1..4) with
     // a0 = (cap - c3) / 5, a1 = cap / 5 + c3 / 20 (N^-1 n_eq of Eqs. 24-25 / 30-31).
     int nee;
+    // Added to a node's storage index to key its stochastic-rounding stream: 0 for a
+    // cavity; for a slab of a cavity split along y, the offset that makes the key the
+    // node's index in the undivided cavity (so a split run rounds as the whole one does).
+    long long seed_off;
     R TwP[4], CwP[4];
     R bT[4], bC[4];
     R uwall[4][2];
@@ -334,13 +338,13 @@ __device__ __forceinline__ void collide_d2q5(R d[5], R Pp, R P, R ux, R uy, R Xx
     d[4] -= -b2 + b3 - b4;
 }
 
-// The full collision of one node, in place on f, g, h (deviations).
-// hist = (T u_x, T u_y, C u_x, C u_y) at the previous step; updated.
-// The D2Q9 part is Eq. 10 written as f* = f - M^-1 [Lambda (m - m_eq) - (I - Lambda/2) S]
-// (only the change is rounded; the density moment is conserved exactly).
+// The collision of one node, in place on the deviations f, g, h: collide_flow (the D2Q9
+// part), then collide_scalars; collide() does both.  hist = (T u_x, T u_y, C u_x, C u_y)
+// at the previous step; updated.  The D2Q9 part is Eq. 10 written as
+// f* = f - M^-1 [Lambda (m - m_eq) - (I - Lambda/2) S] (only the change is rounded; the
+// density moment is conserved exactly).
 template <typename R>
-__device__ __forceinline__ void collide(const Coef<R>& c, R f[9], R g[5], R h[5], R hist[4]) {
-    Macro<R> M = macro(c, f, g, h);
+__device__ __forceinline__ void collide_flow(const Coef<R>& c, const Macro<R>& M, R f[9]) {
     const R ux = M.ux, uy = M.uy, Fx = M.Fx, Fy = M.Fy, rho = M.rho;
     const R ie = c.inv_eps_f;
     // m = M f (Eq. 13), deviation part; m_0 = rho' is not needed
@@ -391,6 +395,14 @@ __device__ __forceinline__ void collide(const Coef<R>& c, R f[9], R g[5], R h[5]
     f[6] -= diag - qx + qy - a8;
     f[7] -= diag - qx - qy + a8;
     f[8] -= diag + qx - qy - a8;
+}
+
+// The two D2Q5 collisions of a node (Eqs. 21-22) with the source of Eq. 27; hist is
+// read and updated.
+template <typename R>
+__device__ __forceinline__ void collide_scalars(const Coef<R>& c, const Macro<R>& M, R g[5], R h[5],
+                                                R hist[4]) {
+    const R ux = M.ux, uy = M.uy;
     // Eq. 27 with d(Phi u)/dt = (Phi u)|t - (Phi u)|t-1 (Sec. 3.2)
     const R T = c.T0 + M.Tp, C = c.C0 + M.Cp;
     const R Tux = T * ux, Tuy = T * uy, Cux = C * ux, Cuy = C * uy;
@@ -401,6 +413,13 @@ __device__ __forceinline__ void collide(const Coef<R>& c, R f[9], R g[5], R h[5]
     hist[3] = Cuy;
     collide_d2q5(g, M.Tp, T, ux, uy, XTx, XTy, c.za1, c.za2, c.za3, c.za4, c.c3T, c.hz1, c.hz2);
     collide_d2q5(h, M.Cp, C, ux, uy, XCx, XCy, c.ed1, c.ed2, c.ed3, c.ed4, c.c3C, c.he1, c.he2);
+}
+
+template <typename R>
+__device__ __forceinline__ void collide(const Coef<R>& c, R f[9], R g[5], R h[5], R hist[4]) {
+    const Macro<R> M = macro(c, f, g, h);
+    collide_flow(c, M, f);
+    collide_scalars(c, M, g, h, hist);
 }
 
 // ---- SplitMix64 (Steele, Lea & Flood 2014): k-th output of a generator seeded with s

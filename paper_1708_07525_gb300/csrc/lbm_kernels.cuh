@@ -350,8 +350,8 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
                Coef<typename Real<S>::type> c) {
     using R = typename Real<S>::type;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= G.nx || j >= G.ny) return;
+    const int j = G.jb + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= G.nx || j >= G.je) return;
     if (INNER && !((unsigned)(i - 1) < (unsigned)(G.nx - 2) && (unsigned)(j - 1) < (unsigned)(G.ny - 2)))
         return;
     R f[9], g[5], h[5], hv[4];
@@ -361,7 +361,7 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
     else
         gather_pull<false, true, EXT>(src, G, i, j, c, f, g, h);
     load_hist(hist, G, self, hv);
-    uint32_t seed = Store<S>::kLow ? node_seed(self, f[0], g[0]) : 0u;
+    uint32_t seed = Store<S>::kLow ? node_seed(self + c.seed_off, f[0], g[0]) : 0u;
     collide_node<EXT>(c, self, G.plane, f, g, h, hv);
     store_ab(dst, G, self, c, f, g, h, seed);
     store_hist(hist, G, self, hv);
@@ -566,12 +566,17 @@ __device__ __forceinline__ W uniform_w(uint64_t seed, uint64_t k) {
 template <typename W>
 __device__ __forceinline__ void initial_TC(const InitSpec& I, const Geom& G, int i, int j, W& Tp,
                                            W& Cp) {
-    const size_t k = (size_t)j * G.nx + i;
     if (I.T_init) {
+        if (j < G.jb || j >= G.je) {          // ghost rows of a slab: never read at t = 0
+            Tp = Cp = W(0);
+            return;
+        }
+        const size_t k = (size_t)(j - G.jb) * G.nx + i;
         Tp = (W)I.T_init[k] - (W)I.T0;
         Cp = (W)I.C_init[k] - (W)I.C0;
     } else {
-        const size_t n = (size_t)G.nx * G.ny;
+        const size_t k = (size_t)(I.key_j0 + j) * G.nx + i;
+        const size_t n = (size_t)G.nx * I.key_ny;
         Tp = (W)I.noise * (W(2) * uniform_w<W>(I.seed, k) - W(1));
         Cp = (W)I.noise * (W(2) * uniform_w<W>(I.seed, n + k) - W(1));
     }
@@ -662,6 +667,31 @@ __global__ void init_kernel(S* __restrict__ buf, typename Real<S>::type* __restr
     store_hist(hist, G, self, hv);
 }
 
+// ---- slabs of a cavity split along y -------------------------------------------------
+// Planes of the populations that cross a horizontal cut between two slabs (Eq. 11 pulls
+// them across it): moving up (e_y = +1) f2, f5, f6, g2, h2; moving down (e_y = -1)
+// f4, f7, f8, g4, h4.
+__host__ __device__ constexpr int halo_plane(int up, int k) {
+    return up ? (k == 0 ? QF + 2 : k == 1 ? QF + 5 : k == 2 ? QF + 6 : k == 3 ? QG + 2 : QH + 2)
+              : (k == 0 ? QF + 4 : k == 1 ? QF + 7 : k == 2 ? QF + 8 : k == 3 ? QG + 4 : QH + 4);
+}
+
+// Copies the five crossing planes of one row between the state and a face buffer
+// face[5][nx] (pack = 1: state -> face, 0: face -> state).  Grid (ceil(nx / 128), 5).
+template <typename S>
+__global__ void __launch_bounds__(128)
+halo_kernel(S* __restrict__ buf, Geom G, int row, int up, S* __restrict__ face, int pack) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (i >= G.nx || k >= 5) return;
+    S* p = buf + (size_t)halo_plane(up, k) * G.plane + (size_t)row * G.pitch + i;
+    S* q = face + (size_t)k * G.nx + i;
+    if (pack)
+        *q = *p;
+    else
+        *p = *q;
+}
+
 // ---- read-outs -----------------------------------------------------------------------
 // Fields at the current level over the window [x0, x0 + w) x [y0, y0 + h):
 // out planes [5][h][w] = ux, uy, T, C, rho (FP64).
@@ -735,7 +765,7 @@ nush_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c, i
             acc[3] += wj * -W.L * (3.0 * C[5] - 4.0 * C[4] + C[3]) / 2.0 / W.dC;
         }
     }
-    for (int j = threadIdx.x; j < G.ny && !W.nee; j += blockDim.x) {
+    for (int j = G.jb + threadIdx.x; j < G.je && !W.nee; j += blockDim.x) {
         R f[9], g[5], h[5];
         double T[4], C[4];
         const int cols[4] = {0, 1, G.nx - 2, G.nx - 1};
@@ -765,7 +795,7 @@ nush_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c, i
     if (threadIdx.x < 4) {
         double s = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
-        out[threadIdx.x] = s / (W.nee ? G.ny - 1.0 : (double)G.ny);
+        out[threadIdx.x] = s / (W.nee ? G.ny - 1.0 : (double)step_rows(G));
     }
 }
 
@@ -854,7 +884,7 @@ residual_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> 
     for (int tx = blockIdx.x; tx < ntx; tx += gridDim.x) {
         const int i = tx * RES_THREADS + threadIdx.x;
         if (i >= G.nx) continue;
-        for (int j = blockIdx.y; j < G.ny; j += gridDim.y) {
+        for (int j = G.jb + blockIdx.y; j < G.je; j += gridDim.y) {
             // all loads first (the snapshot's with the populations), then the stores:
             // a load after a store to the same array waits for nothing, but the
             // compiler keeps them in program order, which would serialise four

@@ -11,18 +11,26 @@
 namespace lbm {
 
 // Geometry of one state: planes of ny rows of `pitch` elements (x fastest).
+// A step updates the rows jb .. je - 1: all rows of a cavity; for a slab of a cavity
+// split along y (lbm_create_slab), the rows between its ghost rows, which hold the
+// neighbouring slabs' boundary populations.
 struct Geom {
     int nx, ny;
     int pitch;       // elements per row, rows start 128-byte aligned
+    int jb;          // first row a step updates
     size_t plane;    // elements per plane = ny * pitch
+    int je;          // one past the last row a step updates
 };
+__host__ __device__ inline int step_rows(const Geom& G) { return G.je - G.jb; }
 
 // How the pre-collision populations of the current level are read.
 enum { GATHER_LOCAL = 0, GATHER_PULL_AB = 1, GATHER_PULL_AA = 2, GATHER_NEE_AB = 3 };
 
 struct InitSpec {
-    const double* T_init;   // device [ny][nx] or NULL (noise)
+    const double* T_init;   // device [je - jb][nx] (the rows a step updates) or NULL (noise)
     const double* C_init;
+    int key_ny, key_j0;     // noise keys (field * key_ny + key_j0 + j) * nx + i: the whole
+                            // cavity's rows and the global row of row 0
     uint64_t seed;
     double noise;
     double T0, C0, sigma, eps, varpi;
@@ -96,11 +104,17 @@ template <typename S>
 cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename Real<S>::type>& c,
                             int mode, void* snap, double* partial, double* out,
                             cudaStream_t st);
+// Copies the five populations of `row` that cross a horizontal cut moving up (up = 1)
+// or down between the state and face[5][nx] (pack = 1: state -> face).
+template <typename S>
+cudaError_t launch_halo(void* buf, const Geom& G, int row, int up, void* face, int pack,
+                        cudaStream_t st);
 // Grid of the residual's first pass: 256-column tiles along x, one row per block
 // along y (each block loops when ny exceeds the grid's y limit).
 inline dim3 residual_grid(const Geom& G) {
     const int ntx = (G.nx + RES_THREADS - 1) / RES_THREADS;
-    const int gy = G.ny < 65535 ? G.ny : 65535;
+    const int rows = step_rows(G);
+    const int gy = rows < 65535 ? rows : 65535;
     return dim3((unsigned)ntx, (unsigned)(gy > 0 ? gy : 1), 1);
 }
 // Slots the first pass folds its block maxima into (atomically); the second pass

@@ -48,6 +48,16 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
                            const Coef<typename Real<S>::type>& c, const LaunchCfg& L) {
     using R = typename Real<S>::type;
     dim3 b(L.bx, L.by), gr = grid_for(G, L.bx, L.by);
+    if (G.jb != 0 || G.je != G.ny) {
+        // a slab of a split cavity: the rows between its ghost rows, one launch with the
+        // general pull (the ghost rows are ordinary neighbours, walls only where real)
+        gr.y = (unsigned)((step_rows(G) + L.by - 1) / L.by);
+        if (c.poro || c.moving)
+            step_ab_kernel<S, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+        else
+            step_ab_kernel<S, false><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
+        return cudaGetLastError();
+    }
     if constexpr (Store<S>::kLow) {
         dim3 gp;
         if (L.pair && !c.nee && !c.poro && !c.moving && pair_grid_ab(G, gp)) {
@@ -200,6 +210,14 @@ cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename 
     return cudaGetLastError();
 }
 
+template <typename S>
+cudaError_t launch_halo(void* buf, const Geom& G, int row, int up, void* face, int pack,
+                        cudaStream_t st) {
+    const dim3 gr((unsigned)((G.nx + 127) / 128), 5, 1);
+    halo_kernel<S><<<gr, 128, 0, st>>>((S*)buf, G, row, up, (S*)face, pack);
+    return cudaGetLastError();
+}
+
 #define LBM_INSTANTIATE(S)                                                                      \
     template cudaError_t launch_init<S>(void*, void*, const Geom&,                             \
                                         const Coef<Real<S>::type>&, const InitSpec&, bool,     \
@@ -218,6 +236,7 @@ cudaError_t launch_residual(const void* buf, const Geom& G, const Coef<typename 
                                            int, const WallSpec&, double*, cudaStream_t);       \
     template cudaError_t launch_residual<S>(const void*, const Geom&,                          \
                                             const Coef<Real<S>::type>&, int, void*, double*,   \
-                                            double*, cudaStream_t);
+                                            double*, cudaStream_t);                            \
+    template cudaError_t launch_halo<S>(void*, const Geom&, int, int, void*, int, cudaStream_t);
 
 }  // namespace lbm

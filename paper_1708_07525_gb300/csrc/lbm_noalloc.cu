@@ -80,6 +80,8 @@ lbm_status lbm_residual_noalloc(lbm_ctx* ctx, double* snapshot, int have_snapsho
     CtxView v;
     if (!ctx || !snapshot || !r || !lbm_ctx_view(ctx, &v))
         return fail(ctx, LBM_ERR_INVALID, "ctx, snapshot and r must be non-NULL");
+    if (v.G.jb != 0 || v.G.je != v.G.ny)   // a slab: its snapshot would include ghost rows
+        return fail(ctx, LBM_ERR_INVALID, "not defined on a slab (use lbm_residual_parts)");
     // the context's device for the whole call: the symbol lookup, the launches on the
     // context's stream and the copy all belong to it
     DeviceGuard dg(v.device);

@@ -149,15 +149,19 @@ __device__ __forceinline__ void store_hist_pair(float* __restrict__ hist, const 
     for (int k = 0; k < 4; ++k) *reinterpret_cast<float2*>(hist + (size_t)k * G.plane + self) = hv[k].v;
 }
 
-// Stores of the pair's post-collision populations: slot q of the pair itself (two-buffer
-// layout, DST_OPP = false) or slot opp(q) (in-place even step, DST_OPP = true).
+// Stores of the pair's post-collision populations, the flow lattice (f) and the two
+// scalar lattices (g, h) apart: slot q of the pair itself (two-buffer layout,
+// DST_OPP = false) or slot opp(q) (in-place even step, DST_OPP = true).
 template <bool DST_OPP, typename S>
-__device__ __forceinline__ void store_pair_self(S* __restrict__ dst, const Geom& G, size_t self, int sr,
-                                                const f2 f[9], const f2 g[5], const f2 h[5],
-                                                uint32_t& state) {
+__device__ __forceinline__ void store_pair_self_f(S* __restrict__ dst, const Geom& G, size_t self, int sr,
+                                                  const f2 f[9], uint32_t& state) {
 #pragma unroll
     for (int q = 0; q < 9; ++q)
         st_pair(dst + (size_t)(QF + (DST_OPP ? opp_of(q) : q)) * G.plane + self, true, f[q], sr, state);
+}
+template <bool DST_OPP, typename S>
+__device__ __forceinline__ void store_pair_self_gh(S* __restrict__ dst, const Geom& G, size_t self, int sr,
+                                                   const f2 g[5], const f2 h[5], uint32_t& state) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const int slot = DST_OPP ? opp_of(q) : q;
@@ -168,14 +172,18 @@ __device__ __forceinline__ void store_pair_self(S* __restrict__ dst, const Geom&
 
 // In-place odd step: slot q of x + e_q (both nodes away from the walls).
 template <typename S>
-__device__ __forceinline__ void store_pair_push(S* __restrict__ buf, const Geom& G, size_t self, int sr,
-                                                const f2 f[9], const f2 g[5], const f2 h[5],
-                                                uint32_t& state) {
+__device__ __forceinline__ void store_pair_push_f(S* __restrict__ buf, const Geom& G, size_t self, int sr,
+                                                  const f2 f[9], uint32_t& state) {
     S* p = buf + self;
 #pragma unroll
     for (int q = 0; q < 9; ++q)
         st_pair(p + ((long long)(QF + q) * (long long)G.plane + ex_of(q) + (long long)ey_of(q) * G.pitch),
                 ex_of(q) == 0, f[q], sr, state);
+}
+template <typename S>
+__device__ __forceinline__ void store_pair_push_gh(S* __restrict__ buf, const Geom& G, size_t self, int sr,
+                                                   const f2 g[5], const f2 h[5], uint32_t& state) {
+    S* p = buf + self;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const long long d = (long long)ex_of(q) + (long long)ey_of(q) * G.pitch;
@@ -190,14 +198,22 @@ __host__ __device__ inline int inner_pairs(int nx) { return nx >= 5 ? (nx - 3) /
 // ---- kernels -------------------------------------------------------------------------
 // Two-buffer pull step of the inner column pairs: block (PAIR_BX, PAIR_BY) over
 // (pairs, rows 1 .. ny - 2).
+// Launch shape: 128 pairs per block, at least 5 blocks per SM (96 registers).  GB300,
+// 4096^2 BF16, us per step (two-buffer / in-place): 64 x 2 threads unbounded (118
+// registers) 342 / 317; 128 x 1 held to 5 blocks 324 / 302 (6 blocks spill: 336 / 315;
+// 4 blocks: 333 / 324).  The two-buffer kernel reads its source through the
+// non-coherent path (nothing writes it during the step): 324 -> 322.
 #ifndef LBM_PAIR_BX
-#define LBM_PAIR_BX 64
+#define LBM_PAIR_BX 128
 #endif
 #ifndef LBM_PAIR_BY
-#define LBM_PAIR_BY 2
+#define LBM_PAIR_BY 1
 #endif
 #ifndef LBM_PAIR_MIN_BLOCKS
-#define LBM_PAIR_MIN_BLOCKS 1
+#define LBM_PAIR_MIN_BLOCKS 5
+#endif
+#ifndef LBM_PAIR_AB_NC
+#define LBM_PAIR_AB_NC true
 #endif
 constexpr int PAIR_BX = LBM_PAIR_BX, PAIR_BY = LBM_PAIR_BY;
 
@@ -210,11 +226,14 @@ step_ab_pair_kernel(const S* __restrict__ src, S* __restrict__ dst, float* __res
     if (m >= inner_pairs(G.nx) || j > G.ny - 2) return;
     const size_t self = (size_t)j * G.pitch + 2 + 2 * m;
     f2 f[9], g[5], h[5], hv[4];
-    gather_pair_pull<false, false>(src, G, self, f, g, h);
+    gather_pair_pull<false, LBM_PAIR_AB_NC>(src, G, self, f, g, h);
     load_hist_pair(hist, G, self, hv);
     uint32_t state = pair_seed(self, f[0], g[0]);
-    collide(c, f, g, h, hv);
-    store_pair_self<false>(dst, G, self, c.sr, f, g, h, state);
+    const Macro<f2> M = macro(c, f, g, h);
+    collide_flow(c, M, f);
+    store_pair_self_f<false>(dst, G, self, c.sr, f, state);   // f's registers free early
+    collide_scalars(c, M, g, h, hv);
+    store_pair_self_gh<false>(dst, G, self, c.sr, g, h, state);
     store_hist_pair(hist, G, self, hv);
 }
 
@@ -231,8 +250,11 @@ step_aa_even_pair_kernel(S* __restrict__ buf, float* __restrict__ hist, Geom G, 
     gather_pair_local(buf, G, self, f, g, h);
     load_hist_pair(hist, G, self, hv);
     uint32_t state = pair_seed(self, f[0], g[0]);
-    collide(c, f, g, h, hv);
-    store_pair_self<true>(buf, G, self, c.sr, f, g, h, state);
+    const Macro<f2> M = macro(c, f, g, h);
+    collide_flow(c, M, f);
+    store_pair_self_f<true>(buf, G, self, c.sr, f, state);
+    collide_scalars(c, M, g, h, hv);
+    store_pair_self_gh<true>(buf, G, self, c.sr, g, h, state);
     store_hist_pair(hist, G, self, hv);
 }
 
@@ -249,8 +271,11 @@ step_aa_odd_pair_kernel(S* __restrict__ buf, float* __restrict__ hist, Geom G, C
     gather_pair_pull<true, true>(buf, G, self, f, g, h);
     load_hist_pair(hist, G, self, hv);
     uint32_t state = pair_seed(self, f[0], g[0]);
-    collide(c, f, g, h, hv);
-    store_pair_push(buf, G, self, c.sr, f, g, h, state);
+    const Macro<f2> M = macro(c, f, g, h);
+    collide_flow(c, M, f);
+    store_pair_push_f(buf, G, self, c.sr, f, state);
+    collide_scalars(c, M, g, h, hv);
+    store_pair_push_gh(buf, G, self, c.sr, g, h, state);
     store_hist_pair(hist, G, self, hv);
 }
 

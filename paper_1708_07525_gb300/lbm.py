@@ -100,6 +100,12 @@ def lib():
             L.lbm_nusselt_sherwood.argtypes = [P, dp]
             L.lbm_residual.argtypes = [P, dp]
             L.lbm_residual_noalloc.argtypes = [P, C.c_void_p, C.c_int, dp]
+            L.lbm_residual_parts.argtypes = [P, dp]
+            L.lbm_create_slab.argtypes = [C.POINTER(lbm_params), C.c_int, C.c_int,
+                                          C.POINTER(lbm_options), C.POINTER(C.c_void_p)]
+            L.lbm_halo_bytes.argtypes = [P, C.POINTER(C.c_size_t)]
+            L.lbm_halo_export.argtypes = [P, C.c_int, C.c_void_p]
+            L.lbm_halo_import.argtypes = [P, C.c_int, C.c_void_p]
             L.lbm_save.argtypes = [P, C.c_void_p, C.POINTER(C.c_size_t)]
             L.lbm_load.argtypes = [P, C.c_void_p, C.c_size_t]
             L.lbm_get_params.argtypes = [P, C.POINTER(lbm_params)]
@@ -114,7 +120,8 @@ def lib():
                          "lbm_nusselt_sherwood_tb", "lbm_create", "lbm_create_raw",
                          "lbm_reset", "lbm_step",
                          "lbm_fields", "lbm_fields_window", "lbm_nusselt_sherwood", "lbm_residual",
-                         "lbm_residual_noalloc", "lbm_save",
+                         "lbm_residual_noalloc", "lbm_residual_parts", "lbm_create_slab",
+                         "lbm_halo_bytes", "lbm_halo_export", "lbm_halo_import", "lbm_save",
                          "lbm_load", "lbm_get_params"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -216,7 +223,9 @@ class Cavity:
                  J=1.0, sigma=1.0, *, params: lbm_params | None = None, precision="f64",
                  layout="ab", Ma=0.0, varpi=0.0, seed=1, noise=1e-3, T_init=None, C_init=None,
                  stream=None, allocator="torch", block=(0, 0), graph_chunk=0,
-                 round_nearest=False, eps_field=None, K_field=None):
+                 round_nearest=False, eps_field=None, K_field=None, slab=None):
+        """slab=(y0, h): the rows [y0, y0 + h) of the cavity given by `params`
+        (lbm_create_slab); exchange faces with halo_export / halo_import."""
         L = lib()
         o = lbm_options()
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -243,7 +252,10 @@ class Cavity:
                 self._keep.append(a)
                 setattr(o, name, _dptr(a))
         h = C.c_void_p()
-        if params is not None:
+        if slab is not None:
+            st = L.lbm_create_slab(C.byref(params), int(slab[0]), int(slab[1]), C.byref(o),
+                                   C.byref(h))
+        elif params is not None:
             st = L.lbm_create_raw(C.byref(params), C.byref(o), C.byref(h))
         else:
             st = L.lbm_create(lbm_grid(int(nx), int(ny)), Ra, Da, eps, Pr, Le, N, J, sigma,
@@ -254,6 +266,8 @@ class Cavity:
         _check(L.lbm_get_params(self.h, C.byref(p)), self.h)
         self.params = p
         self.nx, self.ny = p.nx, p.ny
+        if slab is not None:
+            self.y0, self.ny = int(slab[0]), int(slab[1])
 
     def close(self):
         if getattr(self, "h", None):
@@ -326,6 +340,23 @@ class Cavity:
         _check(lib().lbm_residual_noalloc(self.h, C.c_void_p(int(snapshot_ptr)),
                                           int(bool(have_snapshot)), C.byref(r)), self.h)
         return r.value
+
+    def residual_parts(self) -> np.ndarray:
+        """lbm_residual_parts: max |phi - phi_snap| (4) and max |phi| (4) of u_x, u_y, T, C."""
+        out = np.empty(8)
+        _check(lib().lbm_residual_parts(self.h, _dptr(out)), self.h)
+        return out
+
+    def halo_bytes(self) -> int:
+        n = C.c_size_t()
+        _check(lib().lbm_halo_bytes(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def halo_export(self, side: int, face_ptr: int):
+        _check(lib().lbm_halo_export(self.h, int(side), C.c_void_p(int(face_ptr))), self.h)
+
+    def halo_import(self, side: int, face_ptr: int):
+        _check(lib().lbm_halo_import(self.h, int(side), C.c_void_p(int(face_ptr))), self.h)
 
     def save(self) -> bytes:
         n = C.c_size_t(0)

@@ -118,3 +118,20 @@ def test_derive_lid_nee_matches_the_oracle(oracle_mod):
     assert g.uw[3][0] == o.uw[3][0] == 0.1
     # L = 128 spacings: Re = L U0 / nu, K = Da L^2
     assert abs(g.nu - 128 * 0.1 / 100.0) < 1e-15 and abs(g.K - 0.1 * 128 * 128) < 1e-9
+
+
+def test_slab_misuse_rejected():
+    """A slab of a cavity split along y: rows must lie in the cavity, and slabs take halfway
+    walls, the two-buffer layout and a uniform medium (checked before any device work)."""
+    p = lbm.lbm_derive_params(16, 20, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
+    for y0, h in ((-1, 5), (15, 6), (3, 0)):
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.Cavity(params=p, slab=(y0, h), allocator=None)
+        assert ei.value.status == lbm.ERR_INVALID
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Cavity(params=p, slab=(0, 10), layout="aa", allocator=None)
+    assert ei.value.status == lbm.ERR_INVALID
+    q = lbm.lbm_derive_params_nee(16, 20, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Cavity(params=q, slab=(0, 10), allocator=None)
+    assert ei.value.status == lbm.ERR_INVALID
