@@ -482,23 +482,30 @@ def run_slab(args):
 
 
 def l2_copy_gbs(stream, mb):
-    """Best-of-10 copy bandwidth (read + write bytes) of `mb` MB each way, back to back."""
+    """Best-of-10 copy bandwidth (read + write bytes) of `mb` MB each way, copied back and
+    forth `passes` times inside one launch (paper_1708_07525_gb300/csrc/probe/l2_copy.cu),
+    so that launch gaps do not count."""
+    import ctypes
     import torch
-    n = mb * (1 << 20) // 4
-    a = torch.rand(n, device="cuda")
+    from paper_1708_07525_gb300 import build as B
+    probe = ctypes.CDLL(B.build_probe())
+    probe.probe_l2_copy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    nbytes = mb * (1 << 20)
+    a = torch.rand(nbytes // 4, device="cuda")
     b = torch.empty_like(a)
-    reps = max(10, int(4e9 / (2 * n * 4)))
-    for _ in range(3):
-        b.copy_(a)
+    blocks = torch.cuda.get_device_properties(0).multi_processor_count * 8
+    passes = max(20, int(8e9 / (2 * nbytes)))
+    args = (a.data_ptr(), b.data_ptr(), nbytes, passes, blocks, stream.cuda_stream)
+    assert probe.probe_l2_copy(*args) == 0
     best = 0.0
     for _ in range(10):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(reps):
-            b.copy_(a)
+        assert probe.probe_l2_copy(*args) == 0
         e1.record(stream)
         torch.cuda.synchronize()
-        best = max(best, 2 * n * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        best = max(best, 2 * nbytes * passes / (e0.elapsed_time(e1) / 1e3) / 1e9)
     return best
 
 
@@ -514,7 +521,8 @@ def run_l2peak(args):
     out = {str(mb): l2_copy_gbs(stream, mb) for mb in [int(x) for x in args.l2_mb.split(",")]}
     line = {"metric": "L2-resident copy bandwidth", "mode": "l2peak", "unit": "GB/s",
             "value": max(out.values()), "by_mb_each_way": out,
-            "how": "torch copy_ of float32 buffers (read + write bytes), back to back, CUDA "
+            "how": "copies back and forth between two buffers inside one launch (16-byte "
+                   "loads and stores, 8 blocks of 256 threads per SM), read + write bytes, CUDA "
                    "events, best of 10 rounds",
             "l2_bytes": torch.cuda.get_device_properties(0).L2_cache_size}
     print(json.dumps(line), flush=True)
@@ -657,7 +665,10 @@ def run_serve(args):
     sizes = tuple(int(x) for x in args.serve_sizes.split(","))
     specs = draw_batch(args.requests, seed=5, sizes=sizes)
     insts = [lbm.make_instance(s) for s in specs]
-    cap, check, tol, ntol = args.max_steps, args.check_every, args.serve_tol, args.nush_tol
+    check, tol, ntol = args.check_every, args.serve_tol, args.nush_tol
+    # every time scale in steps grows like the grid width (the mapping of Sec. 4.1 fixes U):
+    # the step cap is --max-steps at 64^2, scaled by L / 64
+    caps = [max(check, int(args.max_steps * s.nx / 64)) for s in specs]
 
     def serve(arrive):
         srv = lbm.Server(args.budget_gb * (1 << 30), max_slots=len(specs), check_every=check,
@@ -669,7 +680,7 @@ def run_serve(args):
             now = time.perf_counter() - t_start
             while pending and arrive[pending[0]] <= now:
                 k = pending.pop(0)
-                srv.submit(insts[k], tol=tol, nush_tol=ntol, max_steps=cap, rid=k)
+                srv.submit(insts[k], tol=tol, nush_tol=ntol, max_steps=caps[k], rid=k)
             active = srv.tick()
             t_now = time.perf_counter() - t_start
             for r in srv.poll():
@@ -694,32 +705,38 @@ def run_serve(args):
 
     fp64_service = [None]
 
-    def alone(precision, budget_s):
+    def alone(precision, budget_s, order):
+        """One request at a time in `order`, until the time budget is spent."""
         res, service = {}, []
         if precision == "f64":
             fp64_service[0] = service
         t0 = time.perf_counter()
-        for k, s in enumerate(specs):
+        for k in order:
             if time.perf_counter() - t0 > budget_s:
                 break
             t1 = time.perf_counter()
-            res[k] = solve_alone(lbm, s, precision, "ab", stream.cuda_stream, tol, ntol, check,
-                                 cap)
+            res[k] = solve_alone(lbm, specs[k], precision, "ab", stream.cuda_stream, tol, ntol,
+                                 check, caps[k])
             torch.cuda.synchronize()
             service.append(time.perf_counter() - t1)
+            res[k]["seconds"] = service[-1]
         secs = time.perf_counter() - t0
-        l = np.array(fifo_latency(arr[:len(service)], service)) if service else np.array([np.nan])
+        done = [k for k in order if k in res]
+        l = (np.array(fifo_latency(arr[done], service)) if done == list(range(len(done)))
+             else np.array([np.nan]))
         return res, secs, l
 
-    same, same_s, same_lat = alone(args.precision, args.plain_budget_s)
+    same, same_s, same_lat = alone(args.precision, args.alone_budget_s, range(len(specs)))
     if args.fp64_cache and os.path.exists(args.fp64_cache):   # the FP64 arm of an earlier run
         with open(args.fp64_cache) as f:
             cached = json.load(f)
         fp64 = {int(k): v for k, v in cached["results"].items()}
         fp64_s = cached["seconds"]
-        fp64_lat = np.array(fifo_latency(arr[:len(fp64)], cached["service"]))
+        fp64_lat = np.array([np.nan])
     else:
-        fp64, fp64_s, fp64_lat = alone("f64", args.plain_budget_s)
+        # smallest grids first, so that the budget covers as many requests as it can
+        order = sorted(range(len(specs)), key=lambda k: (specs[k].nx, k))
+        fp64, fp64_s, fp64_lat = alone("f64", args.plain_budget_s, order)
         if args.fp64_cache:
             with open(args.fp64_cache, "w") as f:
                 json.dump({"results": fp64, "seconds": fp64_s, "service": fp64_service[0]}, f)
@@ -742,6 +759,22 @@ def run_serve(args):
     e_served = errs_vs(fp64, served)
     e_same = errs_vs(fp64, same)
     nodes = {k: s.nx * s.ny for k, s in enumerate(specs)}
+    # FP64 one at a time over the whole prefix, estimated from its measured rate per grid
+    # size (lattice updates per second of the requests it finished; a size it did not reach
+    # takes the rate of the largest size it did)
+    rate64 = {}
+    for k, r in fp64.items():
+        n = specs[k].nx
+        u, t = rate64.get(n, (0.0, 0.0))
+        rate64[n] = (u + nodes[k] * r["steps"], t + r["seconds"])
+    est64 = None
+    if rate64:
+        largest = max(rate64)
+        est64 = 0.0
+        for k in served:
+            n = specs[k].nx if specs[k].nx in rate64 else largest
+            u, t = rate64[n]
+            est64 += nodes[k] * served[k]["steps"] / (u / t)
     line = {
         "metric": METRIC, "mode": "serve", "value": len(specs) / served_s, "unit": "solves/s",
         "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
@@ -750,7 +783,8 @@ def run_serve(args):
                                f"min(0.4, 0.8 min(eps, sigma)), Poisson arrivals at "
                                f"{rate:.3g}/s; every arm stops a request at the first check "
                                f"(every {check} steps) where the residual < {tol} or every "
-                               f"Nu/Sh moved < {ntol} relative, else at {cap} steps",
+                               f"Nu/Sh moved < {ntol} relative, else at {args.max_steps} x L / 64 "
+                               f"steps",
                    "precision": args.precision, "layout": args.layout,
                    "budget_gb": args.budget_gb,
                    "grids": {str(n): sum(1 for s in specs if s.nx == n) for n in sizes},
@@ -766,12 +800,15 @@ def run_serve(args):
             "nush_rel_err_vs_fp64": {"n": int(np.isfinite(e_same).sum()),
                                      "max": float(np.nanmax(e_same)) if np.isfinite(e_same).any() else None}},
         "plain_fp64": {
-            "solves": len(fp64), "seconds": fp64_s, "solves_per_s": len(fp64) / fp64_s,
-            "status": status_counts(fp64),
-            "latency_s": {"p50": pct(fp64_lat, 50), "p99": pct(fp64_lat, 99)}},
+            "solves": len(fp64), "seconds": fp64_s, "status": status_counts(fp64),
+            "order": "smallest grids first, within --plain-budget-s",
+            "grids": {str(n): sum(1 for k in fp64 if specs[k].nx == n) for n in sizes},
+            "glups_by_grid": {str(n): u / t / 1e9 for n, (u, t) in sorted(rate64.items())},
+            "estimated_seconds_for_all_requests": est64,
+            "estimated_solves_per_s": len(specs) / est64 if est64 else None},
         "speedup_vs_one_at_a_time": (len(specs) / served_s) / (len(same) / same_s)
                                     if len(same) == len(specs) else None,
-        "speedup_vs_plain_fp64": (len(specs) / served_s) / (len(fp64) / fp64_s),
+        "speedup_vs_plain_fp64_estimated": est64 / served_s if est64 else None,
         "nush_rel_err_vs_fp64": {"n": int(np.isfinite(e_served).sum()),
                                  "max": float(np.nanmax(e_served)) if np.isfinite(e_served).any() else None,
                                  "median": float(np.nanmedian(e_served)) if np.isfinite(e_served).any() else None,
@@ -961,7 +998,8 @@ def main():
     ap.add_argument("--check-every", type=int, default=500)
     ap.add_argument("--max-steps", type=int, default=300000)
     ap.add_argument("--budget-gb", type=float, default=8.0)
-    ap.add_argument("--plain-budget-s", type=float, default=120.0)
+    ap.add_argument("--plain-budget-s", type=float, default=300.0)
+    ap.add_argument("--alone-budget-s", type=float, default=3600.0)
     ap.add_argument("--partial-out", default="")
     ap.add_argument("--fp64-cache", default="",
                     help="serve: file holding the FP64 one-at-a-time arm (written if absent)")

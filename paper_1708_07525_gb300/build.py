@@ -16,6 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
+PROBE = os.path.join(BUILD, "libprobe.so")     # measurement utility of the benchmark
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]
@@ -46,6 +47,7 @@ def up_to_date() -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
+        build_probe()
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
@@ -73,7 +75,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    build_probe(nv)
     return LIB
+
+
+def build_probe(nv=None) -> str:
+    """libprobe.so: the L2-resident copy probe the benchmark takes its L2 peak from."""
+    src = os.path.join(CSRC, "probe", "l2_copy.cu")
+    if os.path.exists(PROBE) and os.path.getmtime(PROBE) >= os.path.getmtime(src):
+        return PROBE
+    tmp = PROBE + f".tmp{os.getpid()}"
+    cmd = [nv or nvcc()] + ARCH + ["-O3", "-Xcompiler", "-fPIC", "-shared", "-cudart", "static",
+                                   "-o", tmp, src]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE)
+    return PROBE
 
 
 if __name__ == "__main__":
