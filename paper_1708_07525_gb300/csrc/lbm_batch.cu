@@ -194,6 +194,11 @@ struct lbm_batch {
     // L2 temporal blocking: groups of cavities whose working set fits in a share of
     // L2 are advanced `tblock` steps at a time.
     std::vector<std::pair<int, int>> groups;   // [tile_begin, tile_end)
+    // Per group: the slot of its one cavity when that cavity alone exceeds its lane's L2
+    // share (its state streams from HBM whatever the blocking), else -1.  Such a group
+    // runs the single-cavity step kernels over that cavity, whose per-node arithmetic is
+    // the tile kernel's (bit for bit) and which stream HBM faster than 128-node tiles.
+    std::vector<int> group_direct;
     // Groups are independent, so they are dealt round-robin to kLanes streams (the
     // batch's own and kLanes - 1 more): one lane's launches fill the others' wave
     // tails and launch gaps.  The kLanes groups in flight share the L2 budget.
@@ -339,23 +344,33 @@ lbm_status sync_tables(lbm_batch* b) {
     // groups: consecutive cavities while their per-step working set (buffers read
     // and written, history) stays within the L2 budget
     b->groups.clear();
+    b->group_direct.clear();
     {
         size_t ws = 0;
-        int gbeg = 0;
+        int gbeg = 0, members = 0, last = -1;
+        const size_t share = b->l2_budget / lbm_batch::kLanes;
+        auto close = [&](int t_end) {
+            b->groups.push_back({gbeg, t_end});
+            const bool alone_big = members == 1 && ws > share && !b->slots[last].P.nee;
+            b->group_direct.push_back(alone_big ? last : -1);
+        };
         for (int k = 0; k < b->capacity; ++k) {
             const Slot& s = b->slots[k];
             if (!s.used) continue;
             const size_t w = (b->layout == LBM_AA ? 1 : 2) * (size_t)NQ * s.G.plane * esize(b->prec) +
                              (size_t)4 * s.G.plane * sizeof(float);
             const int t0 = b->h_table[k].tile_begin;
-            if (ws > 0 && ws + w > b->l2_budget / lbm_batch::kLanes) {
-                b->groups.push_back({gbeg, t0});
+            if (ws > 0 && ws + w > share) {
+                close(t0);
                 gbeg = t0;
                 ws = 0;
+                members = 0;
             }
             ws += w;
+            members += 1;
+            last = k;
         }
-        if (tiles > gbeg) b->groups.push_back({gbeg, tiles});
+        if (tiles > gbeg) close(tiles);
     }
     if ((size_t)tiles > b->owner_cap) {
         b->dfree(b->d_owner);
@@ -405,6 +420,31 @@ cudaError_t launch_range(lbm_batch* b, int tile_begin, int tile_end, int parity,
     }
 }
 
+// One step of the cavity in slot k with the single-cavity kernels (see group_direct).
+cudaError_t launch_direct(lbm_batch* b, int k, int parity, cudaStream_t st) {
+    const BatchInst<float>& I = b->h_table[k];
+    const int odd = (parity + I.phase) & 1;
+    LaunchCfg L;
+    std::memset(&L, 0, sizeof L);
+    L.bx = 128;
+    L.by = 1;
+    L.stream = st;                 // the ring of a split step runs on the same stream
+    const bool aa = b->layout == LBM_AA;
+    void* src = aa ? I.buf[0] : I.buf[odd];
+    void* dst = aa ? I.buf[0] : I.buf[odd ^ 1];
+    switch (b->prec) {
+        case LBM_F32:
+            return aa ? launch_step_aa<float>(src, I.hist, I.G, I.c, odd != 0, L)
+                      : launch_step_ab<float>(src, dst, I.hist, I.G, I.c, L);
+        case LBM_BF16:
+            return aa ? launch_step_aa<__nv_bfloat16>(src, I.hist, I.G, I.c, odd != 0, L)
+                      : launch_step_ab<__nv_bfloat16>(src, dst, I.hist, I.G, I.c, L);
+        default:
+            return aa ? launch_step_aa<__half>(src, I.hist, I.G, I.c, odd != 0, L)
+                      : launch_step_ab<__half>(src, dst, I.hist, I.G, I.c, L);
+    }
+}
+
 void destroy_lanes(lbm_batch* b) {
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     for (int l = 0; l + 1 < lbm_batch::kLanes; ++l) {
@@ -434,8 +474,10 @@ cudaError_t launch_block(lbm_batch* b, int k) {
         const auto& g = b->groups[gi];
         const int l = (int)(gi % (size_t)lanes);
         const cudaStream_t st = l == 0 ? b->stream : b->lane[l - 1];
+        const int direct = b->group_direct[gi];
         for (int s = 0; s < k && e == cudaSuccess; ++s)
-            e = launch_range(b, g.first, g.second, (int)((b->t + s) & 1), st);
+            e = direct >= 0 ? launch_direct(b, direct, (int)((b->t + s) & 1), st)
+                            : launch_range(b, g.first, g.second, (int)((b->t + s) & 1), st);
     }
     // join even after a failed launch, so that a capture is never left forked
     for (int l = 1; l < lanes; ++l) {

@@ -71,21 +71,8 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
             step_ab_edge_kernel<S><<<(unsigned)((ne + 127) / 128), 128, 0, rs>>>(
                 (const S*)src, (S*)dst, (float*)hist, G, c);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-#if LBM_PAIR_PERSISTENT
-            {
-                int dev = 0, sms = 0;
-                cudaGetDevice(&dev);
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-                const long long ntiles = (long long)((inner_pairs(G.nx) + PAIR_BX - 1) / PAIR_BX) * (G.ny - 2);
-                const long long nb = std::min<long long>(ntiles, (long long)sms * LBM_PAIR_MIN_BLOCKS);
-                static_assert(PAIR_BY == 1, "the persistent kernel takes one row per tile");
-                step_ab_pair_persistent_kernel<S><<<(unsigned)nb, PAIR_BX, 0, L.stream>>>(
-                    (const S*)src, (S*)dst, (float*)hist, G, *L.pair);
-            }
-#else
             step_ab_pair_kernel<S><<<gp, dim3(PAIR_BX, PAIR_BY), 0, L.stream>>>(
                 (const S*)src, (S*)dst, (float*)hist, G, *L.pair);
-#endif
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             return ring_join(L);
         }

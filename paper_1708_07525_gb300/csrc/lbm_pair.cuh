@@ -202,7 +202,9 @@ __host__ __device__ inline int inner_pairs(int nx) { return nx >= 5 ? (nx - 3) /
 // 4096^2 BF16, us per step (two-buffer / in-place): 64 x 2 threads unbounded (118
 // registers) 342 / 317; 128 x 1 held to 5 blocks 324 / 302 (6 blocks spill: 336 / 315;
 // 4 blocks: 333 / 324).  The two-buffer kernel reads its source through the
-// non-coherent path (nothing writes it during the step): 324 -> 322.
+// non-coherent path (nothing writes it during the step): 324 -> 322.  A persistent form
+// that asked L2 for each block's next tile (prefetch.global.L2, a line per thread) ran
+// slower (408 us).
 #ifndef LBM_PAIR_BX
 #define LBM_PAIR_BX 128
 #endif
@@ -215,9 +217,7 @@ __host__ __device__ inline int inner_pairs(int nx) { return nx >= 5 ? (nx - 3) /
 #ifndef LBM_PAIR_AB_NC
 #define LBM_PAIR_AB_NC true
 #endif
-#ifndef LBM_PAIR_PERSISTENT
-#define LBM_PAIR_PERSISTENT 0
-#endif
+
 constexpr int PAIR_BX = LBM_PAIR_BX, PAIR_BY = LBM_PAIR_BY;
 
 template <typename S>
@@ -238,67 +238,6 @@ step_ab_pair_kernel(const S* __restrict__ src, S* __restrict__ dst, float* __res
     collide_scalars(c, M, g, h, hv);
     store_pair_self_gh<false>(dst, G, self, c.sr, g, h, state);
     store_hist_pair(hist, G, self, hv);
-}
-
-// The same step as a persistent loop over tiles (one row, PAIR_BX column pairs), each block
-// taking every gridDim.x-th tile, that first asks L2 for the block's next tile: the 128-byte
-// lines of its 19 source row segments and 4 history row segments (prefetch.global.L2, a
-// line per thread), so that the demand loads of the next tile find their lines in L2.
-// With 5 blocks of 128 threads per SM (96 registers) the demand loads alone keep too few
-// bytes in flight to reach the DRAM bandwidth.
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-template <typename S>
-__device__ __forceinline__ void prefetch_pair_tile(const S* __restrict__ src, const float* __restrict__ hist,
-                                                   const Geom& G, int j, int x0) {
-    constexpr int EL = 128 / sizeof(S);                 // elements per line
-    constexpr int NL = (2 * PAIR_BX + EL - 1) / EL + 1;  // lines per row segment
-    constexpr int HL = (2 * PAIR_BX * 4 + 127) / 128 + 1;
-    const int lines_per_row = (int)((G.pitch * sizeof(S)) / 128);
-    const int hlines_per_row = (int)((G.pitch * 4) / 128);
-    const int first = x0 / EL, hfirst = (x0 * 4) / 128;
-    for (int L = threadIdx.x; L < 19 * NL + 4 * HL; L += blockDim.x) {
-        if (L < 19 * NL) {
-            const int q = L / NL, part = first + L % NL;
-            if (part >= lines_per_row) continue;
-            const int ey = q < 9 ? ey_of(q) : ey_of(q < 14 ? q - 9 : q - 14);
-            prefetch_l2(src + (size_t)q * G.plane + (size_t)(j - ey) * G.pitch + (size_t)part * EL);
-        } else {
-            const int k = (L - 19 * NL) / HL, part = hfirst + (L - 19 * NL) % HL;
-            if (part >= hlines_per_row) continue;
-            prefetch_l2(hist + (size_t)k * G.plane + (size_t)j * G.pitch + (size_t)part * 32);
-        }
-    }
-}
-
-template <typename S>
-__global__ void __launch_bounds__(PAIR_BX * PAIR_BY, LBM_PAIR_MIN_BLOCKS)
-step_ab_pair_persistent_kernel(const S* __restrict__ src, S* __restrict__ dst, float* __restrict__ hist,
-                               Geom G, Coef<f2> c) {
-    const int np = inner_pairs(G.nx);
-    const int tiles_x = (np + PAIR_BX - 1) / PAIR_BX;
-    const long long ntiles = (long long)tiles_x * (G.ny - 2);
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long nt = t + gridDim.x;
-        if (nt < ntiles)
-            prefetch_pair_tile(src, hist, G, 1 + (int)(nt / tiles_x), 2 + 2 * PAIR_BX * (int)(nt % tiles_x));
-        const int j = 1 + (int)(t / tiles_x);
-        const int m = PAIR_BX * (int)(t % tiles_x) + threadIdx.x;
-        if (m >= np) continue;
-        const size_t self = (size_t)j * G.pitch + 2 + 2 * m;
-        f2 f[9], g[5], h[5], hv[4];
-        gather_pair_pull<false, LBM_PAIR_AB_NC>(src, G, self, f, g, h);
-        load_hist_pair(hist, G, self, hv);
-        uint32_t state = pair_seed(self, f[0], g[0]);
-        const Macro<f2> M = macro(c, f, g, h);
-        collide_flow(c, M, f);
-        store_pair_self_f<false>(dst, G, self, c.sr, f, state);
-        collide_scalars(c, M, g, h, hv);
-        store_pair_self_gh<false>(dst, G, self, c.sr, g, h, state);
-        store_hist_pair(hist, G, self, hv);
-    }
 }
 
 // In-place even step of every column pair (even nx): block (PAIR_BX, PAIR_BY) over

@@ -178,3 +178,28 @@ def test_wall_node_cavity_rejected_by_in_place_batches():
     with pytest.raises(lbm.LbmError) as ei:
         lbm.Batch([lbm.make_instance(params=pc)], precision="f32", layout="aa")
     assert ei.value.status == lbm.ERR_INVALID
+
+
+@pytest.mark.parametrize("precision,layout", [("f32", "ab"), ("f32", "aa"), ("bf16", "ab")])
+def test_cavity_beyond_its_l2_share_runs_the_single_cavity_kernels(precision, layout):
+    """A 512^2 cavity (44 MB of FP32 state, more than a lane's quarter of L2) is stepped by
+    the single-cavity kernels inside the batch: bit for bit the single-cavity run (one node
+    per thread), while the small cavities beside it keep their tile kernel."""
+    big = CavitySpec(512, 512, Ra=1e5, Da=1e-2, eps=0.6, Le=2.0, N=-1.0, seed=21, noise=0.02)
+    b = lbm.Batch([lbm.make_instance(MIX[0]), lbm.make_instance(big), lbm.make_instance(MIX[2])],
+                  precision=precision, layout=layout)
+    b.step(101)
+    if precision == "f32":
+        single = lbm.Cavity(*big.args(), precision=precision, layout=layout, seed=big.seed,
+                            noise=big.noise)
+    else:   # the one-node 16-bit kernels (a one-slab cavity runs them, see lbm_create_slab)
+        single = lbm.Cavity(params=lbm.lbm_derive_params(*big.args()), slab=(0, big.ny),
+                            precision=precision, layout=layout, seed=big.seed, noise=big.noise)
+    single.step(101)
+    fb, fs = b.fields(1), single.fields()
+    for key in KEYS:
+        assert np.array_equal(fb[key], fs[key]), key
+    alone = lbm.Batch([lbm.make_instance(MIX[2])], precision=precision, layout=layout)
+    alone.step(101)
+    for key in KEYS:
+        assert np.array_equal(alone.fields(0)[key], b.fields(2)[key]), key
