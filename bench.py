@@ -197,7 +197,9 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"porous cavity {n}x{n}, Ra=1e5 Da=1e-3 eps=0.4 Pr=1 Le=5 N=-1",
+        "config": {"workload": f"porous cavity {n}x{n}, Ra=1e5 Da=1e-3 eps=0.4 Pr=1 Le=5 N=-1, "
+                               f"halfway walls",
+                   "storage": "f64 (the oracle: FP64 throughout, push streaming)",
                    "nx": n, "ny": n, "bench_step": f"{per_step} time step(s) of the CPU oracle"},
         "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": O.get_threads(), "kind": "oracle",
                          "sample": f"{n}x{n} cavity, {per_step} time step(s) per bench step"},
@@ -321,9 +323,10 @@ def run_ours(args):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {
-            "workload": f"porous cavity {n}x{n}, Ra=1e5 Da=1e-3 eps=0.4 Pr=1 Le=5 N=-1, "
-                        f"{args.precision} {'two-buffer pull' if args.layout == 'ab' else 'in-place AA'}"
+            "workload": f"porous cavity {n}x{n}, Ra=1e5 Da=1e-3 eps=0.4 Pr=1 Le=5 N=-1"
                         + (", wall nodes (Sec. 3.3)" if args.walls == "nee" else ", halfway walls"),
+            "storage": f"{args.precision} "
+                       f"{'two-buffer pull' if args.layout == 'ab' else 'in-place AA'}",
             "nx": n, "ny": n, "time_steps_per_bench_step": k,
             "bench_step": f"{k} fused time steps + FP64 Nu/Sh reduction + residual",
             "l2": "state larger than L2 (no flush needed)" if nodes * bpn / 2 > 129e6
