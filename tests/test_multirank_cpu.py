@@ -122,3 +122,13 @@ def test_two_rank_slab_split_equals_single_rank_oracle():
     for k in ("ux", "uy", "T", "C", "rho"):
         got = np.concatenate([parts[0][k], parts[1][k]], axis=0)
         assert np.array_equal(got, fr[k]), k
+
+
+def test_fifo_latency_of_one_at_a_time_service():
+    """The one-at-a-time arm's latencies: FIFO service of one request at a time, each
+    starting when it has arrived and the previous one is done."""
+    import bench
+    arrive = [0.0, 1.0, 1.5, 10.0]
+    service = [2.0, 1.0, 3.0, 0.5]
+    # finishes: 2.0, 3.0, 6.0, 10.5
+    assert bench.fifo_latency(arrive, service) == [2.0, 2.0, 4.5, 0.5]
