@@ -614,7 +614,7 @@ def run_batch(args):
 
 
 def solve_alone(lbm, spec, precision, layout, stream, tol, nush_tol, check, cap):
-    """One cavity solve on its own (one fused launch per time step, CUDA graphs), stopped
+    """One cavity solve on its own (the single-cavity step kernels, CUDA graphs), stopped
     by the server's rule: at a check every `check` steps it is steady if the residual
     over those steps is below tol, or (from the second check on) if every Nu_L, Sh_L,
     Nu_R, Sh_R moved by less than nush_tol relative since the previous check; past `cap`

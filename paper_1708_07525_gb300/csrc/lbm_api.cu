@@ -749,6 +749,7 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
 lbm_status lbm_create_slab(const lbm_params* params, int y0, int h, const lbm_options* opt,
                            lbm_ctx** out) {
     if (h < 1) {
+        if (out) *out = nullptr;
         set_global_error("lbm_create_slab: a slab needs at least one row");
         return LBM_ERR_INVALID;
     }

@@ -20,8 +20,9 @@
 
 namespace lbm {
 
-// Pair loads and stores of 16-bit storage.  ld2 / st2 address two consecutive values
-// at an even element offset (4-byte aligned); ld1 / st1 one value.
+// Pair loads and conversions of 16-bit storage.  ld2 reads two consecutive values at an
+// even element offset (one 4-byte aligned word), ld1 one value; widen / narrow convert a
+// word of two 16-bit values to and from an f2 (the first node in the low half).
 template <typename S> struct Pair;
 
 template <> struct Pair<__nv_bfloat16> {
@@ -83,8 +84,9 @@ __device__ __forceinline__ uint32_t pair_seed(size_t self, f2 a, f2 b) {
     return mix32(x ^ mix32(y ^ mix32((uint32_t)self ^ (uint32_t)(self >> 32) * 0x27D4EB2Fu)));
 }
 
-// Value pair at element offset `off` from p0 (p0 + off is the first node's value);
-// `aligned`: off is even (the source / target column pair is the node pair itself).
+// The values at p and p + 1 (the first and the second node's); `aligned`: p is at an even
+// element offset (the source or target column pair is the node pair itself), so that one
+// 32-bit word holds both.
 template <typename S, bool NC>
 __device__ __forceinline__ f2 ld_pair(const S* p, bool aligned) {
     if (aligned) return NC ? Pair<S>::ld2_nc(p) : Pair<S>::ld2(p);
@@ -159,7 +161,7 @@ __device__ __forceinline__ void store_hist_pair(float* __restrict__ hist, const 
 
 // Stores of the pair's post-collision populations, the flow lattice (f) and the two
 // scalar lattices (g, h) apart: slot q of the pair itself (two-buffer layout,
-// DST_OPP = false) or slot opp(q) (in-place even step, DST_OPP = true).
+// DST_OPP = false, streaming stores) or slot opp(q) (in-place even step, DST_OPP = true).
 template <bool DST_OPP, typename S>
 __device__ __forceinline__ void store_pair_self_f(S* __restrict__ dst, const Geom& G, size_t self, int sr,
                                                   const f2 f[9], uint32_t& state) {
