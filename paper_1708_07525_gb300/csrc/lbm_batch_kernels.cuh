@@ -43,10 +43,7 @@ __device__ __forceinline__ void load_inst(const BatchInst<R>* __restrict__ table
 // NEE = true: the batch holds cavities with wall nodes (Sec. 3.3); their nodes gather
 // through the rebuild (two-buffer layout only).
 template <typename S, bool AA, bool NEE = false>
-#ifndef LBM_BATCH_LOOP_MIN_BLOCKS
-#define LBM_BATCH_LOOP_MIN_BLOCKS 4
-#endif
-__global__ void __launch_bounds__(BATCH_THREADS, LBM_BATCH_LOOP_MIN_BLOCKS)
+__global__ void __launch_bounds__(BATCH_THREADS, 4)
 batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
                   const int* __restrict__ tile_owner, int tile_begin, int tile_end, int parity) {
     using R = typename Real<S>::type;
