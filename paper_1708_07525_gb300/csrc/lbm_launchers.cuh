@@ -35,7 +35,7 @@ cudaError_t launch_init(void* buf, void* hist, const Geom& G, const Coef<typenam
 inline bool pair_grid_ab(const Geom& G, dim3& gr) {
     const int np = inner_pairs(G.nx), rows = G.ny - 2;
     if (G.nx < 8 || rows < 1 || np < 1) return false;
-    gr = dim3((unsigned)((np + PAIR_BX - 1) / PAIR_BX), (unsigned)((rows + PAIR_BY - 1) / PAIR_BY), 1);
+    gr = dim3((unsigned)((np + PAIR_BX) / PAIR_BX), (unsigned)((rows + PAIR_BY - 1) / PAIR_BY), 1);
     return gr.y <= 65535u;
 }
 inline bool pair_grid_aa_even(const Geom& G, dim3& gr) {

@@ -206,16 +206,29 @@ __device__ __forceinline__ void store_pair_push_gh(S* __restrict__ buf, const Ge
 // Number of inner column pairs (2, 3), (4, 5), ... with both nodes in 1 .. nx - 2.
 __host__ __device__ inline int inner_pairs(int nx) { return nx >= 5 ? (nx - 3) / 2 : 0; }
 
+// Thread m of a row of the inner-pair kernels takes the column pair (2m, 2m + 1); m = 0
+// (the edge columns 0 and 1) has no work.  With rows starting on 128-byte lines, a warp's
+// 32 pairs then cover whole lines of every 16-bit plane (128 B) and of the FP32 history
+// (256 B); numbered from column 2 instead, each warp's words started 4 bytes into a line,
+// so the first sector of every line of the two-buffer destination was written by two
+// warps in two parts.
+__device__ __forceinline__ bool inner_pair_of(const Geom& G, int& m, int& j) {
+    m = blockIdx.x * blockDim.x + threadIdx.x;
+    j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    return m >= 1 && m <= inner_pairs(G.nx) && j <= G.ny - 2;
+}
+
 // ---- kernels -------------------------------------------------------------------------
 // Two-buffer pull step of the inner column pairs: block (PAIR_BX, PAIR_BY) over
-// (pairs, rows 1 .. ny - 2).
+// (1 + pairs, rows 1 .. ny - 2), the first thread of a row idle (inner_pair_of).
 // Launch shape: 128 pairs per block, at least 5 blocks per SM (96 registers).  GB300,
 // 4096^2 BF16, us per step (two-buffer / in-place): 64 x 2 threads unbounded (118
 // registers) 342 / 317; 128 x 1 held to 5 blocks 324 / 302 (6 blocks spill: 336 / 315;
 // 4 blocks: 333 / 324).  The two-buffer kernel reads its source through the
 // non-coherent path (nothing writes it during the step): 324 -> 322.  A persistent form
 // that asked L2 for each block's next tile (prefetch.global.L2, a line per thread) ran
-// slower (408 us).
+// slower (408 us).  Those figures predate the line-aligned numbering of inner_pair_of(),
+// which with the streaming stores took the two sides to 303.5 / 300.1 us.
 #ifndef LBM_PAIR_BX
 #define LBM_PAIR_BX 128
 #endif
@@ -235,10 +248,9 @@ template <typename S>
 __global__ void __launch_bounds__(PAIR_BX * PAIR_BY, LBM_PAIR_MIN_BLOCKS)
 step_ab_pair_kernel(const S* __restrict__ src, S* __restrict__ dst, float* __restrict__ hist, Geom G,
                     Coef<f2> c) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (m >= inner_pairs(G.nx) || j > G.ny - 2) return;
-    const size_t self = (size_t)j * G.pitch + 2 + 2 * m;
+    int m, j;
+    if (!inner_pair_of(G, m, j)) return;
+    const size_t self = (size_t)j * G.pitch + 2 * m;
     f2 f[9], g[5], h[5], hv[4];
     gather_pair_pull<false, LBM_PAIR_AB_NC>(src, G, self, f, g, h);
     load_hist_pair(hist, G, self, hv);
@@ -277,10 +289,9 @@ step_aa_even_pair_kernel(S* __restrict__ buf, float* __restrict__ hist, Geom G, 
 template <typename S>
 __global__ void __launch_bounds__(PAIR_BX * PAIR_BY, LBM_PAIR_MIN_BLOCKS)
 step_aa_odd_pair_kernel(S* __restrict__ buf, float* __restrict__ hist, Geom G, Coef<f2> c) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (m >= inner_pairs(G.nx) || j > G.ny - 2) return;
-    const size_t self = (size_t)j * G.pitch + 2 + 2 * m;
+    int m, j;
+    if (!inner_pair_of(G, m, j)) return;
+    const size_t self = (size_t)j * G.pitch + 2 * m;
     f2 f[9], g[5], h[5], hv[4];
     gather_pair_pull<true, true>(buf, G, self, f, g, h);
     load_hist_pair(hist, G, self, hv);
