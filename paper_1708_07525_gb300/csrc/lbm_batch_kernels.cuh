@@ -109,9 +109,11 @@ batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
                    const int* __restrict__ tile_owner, int tile_begin, int parity) {
     using R = typename Real<S>::type;
     __shared__ BatchInst<R> I;
+    pdl_trigger();                            // launched by launch_pdl() (launch_batch_step)
     const int tile = tile_begin + blockIdx.x;
-    load_inst(table, tile_owner[tile], I);
+    load_inst(table, tile_owner[tile], I);    // only host copies write the table and owners
     __syncthreads();
+    pdl_wait();                               // the previous step's writes are visible
     if (!I.active) return;
     const int local = tile - I.tile_begin;
     const int ty = local / I.tiles_x, tx = local - ty * I.tiles_x;

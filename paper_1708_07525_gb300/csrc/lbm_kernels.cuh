@@ -6,6 +6,38 @@
 
 namespace lbm {
 
+// ---- programmatic dependent launch ----------------------------------------------------
+// A kernel launched by launch_pdl() may be scheduled while the kernel before it on the
+// same stream is still running.  pdl_trigger() at the start of every CTA lets the next
+// launch begin once all CTAs of this one have started; pdl_wait() holds a CTA until the
+// launch before it has completed and its writes are visible.  A kernel that waits before
+// its first access to the state, in every thread, and reads before that only what no
+// kernel writes, gives the results of ordinary stream order, and it completes only after
+// the launch before it.  Under an ordinary launch (also what launch_pdl() makes on the
+// legacy default stream, with its implicit synchronisation) both instructions return at
+// once.
+#ifndef LBM_PDL
+#define LBM_PDL 1
+#endif
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed =
+        LBM_PDL && st != nullptr && st != cudaStreamLegacy ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Which wall a link crosses.  Sides: 0 left (x = 0), 1 right (x = nx),
 // 2 bottom (y = 0), 3 top (y = ny).
 // A population pulled along direction q from x - e_q crosses the wall behind it:
@@ -349,6 +381,8 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
                typename Real<S>::type* __restrict__ hist, Geom G,
                Coef<typename Real<S>::type> c) {
     using R = typename Real<S>::type;
+    pdl_trigger();
+    pdl_wait();                                // launched by launch_pdl() in one-kernel steps
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = G.jb + blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= G.nx || j >= G.je) return;
@@ -472,6 +506,8 @@ __global__ void __launch_bounds__(256)
 step_aa_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
                Coef<typename Real<S>::type> c) {
     using R = typename Real<S>::type;
+    pdl_trigger();
+    pdl_wait();                                // launched by launch_pdl()
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= G.nx || j >= G.ny) return;

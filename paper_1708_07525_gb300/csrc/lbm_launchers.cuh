@@ -113,12 +113,24 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
             step_ab_kernel<S, false, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         return ring_join(L);
-    } else if (c.poro || c.moving)
-        step_ab_kernel<S, true><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
-    else
-        step_ab_kernel<S, false><<<gr, b, 0, L.stream>>>((const S*)src, (S*)dst, (R*)hist, G, c);
-    return cudaGetLastError();
+    }
+    // one kernel per step: a programmatic dependent launch, so that this step's CTAs are
+    // placed while the step before drains
+    if (c.poro || c.moving)
+        return launch_pdl(step_ab_kernel<S, true>, gr, b, L.stream, (const S*)src, (S*)dst, (R*)hist, G, c);
+    return launch_pdl(step_ab_kernel<S, false>, gr, b, L.stream, (const S*)src, (S*)dst, (R*)hist, G, c);
 }
+
+// With FP32 arithmetic the in-place odd step runs as two launches (inner nodes without
+// wall logic, and the ring of outermost nodes on a second stream) from this many nodes
+// on, below it as one kernel with the wall logic: in small cavities the second launch and
+// its fork / join cost more than the lighter inner kernel saves.  GB300, FP32, us per step
+// over alternating odd and even steps (one kernel / split): 128^2 2.5 / 4.6, 256^2 2.9 / 4.9, 512^2
+// 6.9 / 7.8, 1024^2 28.2 / 27.6, 2048^2 121.3 / 117.2.  FP64 splits at every size (128^2
+// 33.1 / 13.5 us, 1024^2 507.5 / 502.3).
+#ifndef LBM_AA_SPLIT_MIN_NODES
+#define LBM_AA_SPLIT_MIN_NODES (1LL << 19)
+#endif
 
 template <typename S>
 cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
@@ -146,7 +158,8 @@ cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
             return ring_join(L);
         }
     }
-    if (odd && G.nx >= 3 && G.ny >= 3) {
+    const long long split_min = std::is_same<R, double>::value ? 0 : LBM_AA_SPLIT_MIN_NODES;
+    if (odd && G.nx >= 3 && G.ny >= 3 && (long long)G.nx * G.ny >= split_min) {
         // the ring of outermost nodes beside the inner nodes (no wall logic); the two
         // launches touch disjoint locations
         cudaStream_t rs;
@@ -165,15 +178,12 @@ cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
             step_aa_odd_inner_kernel<S, false><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         return ring_join(L);
-    } else if (odd && ext)
-        step_aa_kernel<S, true, true><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
-    else if (odd)
-        step_aa_kernel<S, true, false><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
-    else if (ext)
-        step_aa_kernel<S, false, true><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
-    else
-        step_aa_kernel<S, false, false><<<gr, b, 0, L.stream>>>((S*)buf, (R*)hist, G, c);
-    return cudaGetLastError();
+    }
+    // one kernel per step: a programmatic dependent launch, as in launch_step_ab
+    if (odd && ext) return launch_pdl(step_aa_kernel<S, true, true>, gr, b, L.stream, (S*)buf, (R*)hist, G, c);
+    if (odd) return launch_pdl(step_aa_kernel<S, true, false>, gr, b, L.stream, (S*)buf, (R*)hist, G, c);
+    if (ext) return launch_pdl(step_aa_kernel<S, false, true>, gr, b, L.stream, (S*)buf, (R*)hist, G, c);
+    return launch_pdl(step_aa_kernel<S, false, false>, gr, b, L.stream, (S*)buf, (R*)hist, G, c);
 }
 
 template <typename S>
