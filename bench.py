@@ -339,7 +339,8 @@ def run_ours(args):
                      "kernel": (f"step_ab_kernel<{args.precision}> (inner nodes) + nee_ring_kernel"
                                 if args.walls == "nee"
                                 else (f"step_{args.layout}_pair kernels<{args.precision}> (two "
-                                      f"nodes per thread) + edge kernel on a second stream"
+                                      f"nodes per thread; edge nodes one per thread in the "
+                                      f"same launch)"
                                       if args.precision in ("bf16", "f16")
                                       else f"step_{args.layout}_kernel<{args.precision}>")),
                      "kernel_us_per_launch": kernel_ms * 1e3,

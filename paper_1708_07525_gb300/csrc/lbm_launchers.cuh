@@ -32,11 +32,18 @@ cudaError_t launch_init(void* buf, void* hist, const Geom& G, const Coef<typenam
 
 // Grids of the two-nodes-per-thread kernels (lbm_pair.cuh); false if the cavity does
 // not take them (too small, or too many rows for one launch).
-inline bool pair_grid_ab(const Geom& G, dim3& gr) {
+// The pull grid: erows block rows of edge nodes, then the rows of inner pairs.
+inline bool pair_grid_ab(const Geom& G, dim3& gr, int& erows) {
     const int np = inner_pairs(G.nx), rows = G.ny - 2;
     if (G.nx < 8 || rows < 1 || np < 1) return false;
-    gr = dim3((unsigned)((np + PAIR_BX) / PAIR_BX), (unsigned)((rows + PAIR_BY - 1) / PAIR_BY), 1);
-    return gr.y <= 65535u;
+    const long long gx = (np + PAIR_BX) / PAIR_BX;
+    const long long eb = (edge_count(G) + PAIR_BX * PAIR_BY - 1) / (PAIR_BX * PAIR_BY);
+    const long long er = (eb + gx - 1) / gx;
+    const long long gy = (rows + PAIR_BY - 1) / PAIR_BY + er;
+    if (gy > 65535) return false;
+    erows = (int)er;
+    gr = dim3((unsigned)gx, (unsigned)gy, 1);
+    return true;
 }
 inline bool pair_grid_aa_even(const Geom& G, dim3& gr) {
     if (G.nx & 1) return false;
@@ -61,21 +68,12 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
     }
     if constexpr (Store<S>::kLow) {
         dim3 gp;
-        if (L.pair && !c.nee && !c.poro && !c.moving && pair_grid_ab(G, gp)) {
-            // inner column pairs two nodes per thread, the edge set one node per thread
-            // on the second stream (disjoint destinations)
-            cudaStream_t rs;
-            cudaError_t e = ring_fork(L, &rs);
-            if (e != cudaSuccess) return e;
-            const long long ne = edge_count(G);
-            step_ab_edge_kernel<S><<<(unsigned)((ne + 127) / 128), 128, 0, rs>>>(
-                (const S*)src, (S*)dst, (float*)hist, G, c);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            step_ab_pair_kernel<S><<<gp, dim3(PAIR_BX, PAIR_BY), 0, L.stream>>>(
-                (const S*)src, (S*)dst, (float*)hist, G, *L.pair);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            return ring_join(L);
-        }
+        int erows = 0;
+        if (L.pair && !c.nee && !c.poro && !c.moving && pair_grid_ab(G, gp, erows))
+            // inner column pairs two nodes per thread, the edge set one node per thread,
+            // in one programmatic dependent launch
+            return launch_pdl(step_ab_pair_kernel<S>, gp, dim3(PAIR_BX, PAIR_BY), L.stream, (const S*)src,
+                              (S*)dst, (float*)hist, G, *L.pair, c, erows);
     }
     if (c.nee) {
         // the ring of wall nodes: the rebuild (Sec. 3.3); inner nodes: the plain pull
@@ -140,22 +138,14 @@ cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
     const bool ext = c.poro || c.moving;
     if constexpr (Store<S>::kLow) {
         dim3 gp, ge;
-        if (L.pair && !ext && pair_grid_ab(G, gp) && pair_grid_aa_even(G, ge)) {
+        int erows = 0;
+        if (L.pair && !ext && pair_grid_ab(G, gp, erows) && pair_grid_aa_even(G, ge)) {
             const dim3 pb(PAIR_BX, PAIR_BY);
-            if (!odd) {
-                step_aa_even_pair_kernel<S><<<ge, pb, 0, L.stream>>>((S*)buf, (float*)hist, G, *L.pair);
-                return cudaGetLastError();
-            }
-            cudaStream_t rs;
-            cudaError_t e = ring_fork(L, &rs);
-            if (e != cudaSuccess) return e;
-            const long long ne = edge_count(G);
-            step_aa_odd_edge_kernel<S><<<(unsigned)((ne + 127) / 128), 128, 0, rs>>>(
-                (S*)buf, (float*)hist, G, c);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            step_aa_odd_pair_kernel<S><<<gp, pb, 0, L.stream>>>((S*)buf, (float*)hist, G, *L.pair);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            return ring_join(L);
+            if (!odd)
+                return launch_pdl(step_aa_even_pair_kernel<S>, ge, pb, L.stream, (S*)buf, (float*)hist, G,
+                                  *L.pair);
+            return launch_pdl(step_aa_odd_pair_kernel<S>, gp, pb, L.stream, (S*)buf, (float*)hist, G,
+                              *L.pair, c, erows);
         }
     }
     const long long split_min = std::is_same<R, double>::value ? 0 : LBM_AA_SPLIT_MIN_NODES;

@@ -13,8 +13,10 @@
 // Only nodes away from the walls run here (every neighbour in the cavity): the inner
 // column pairs (2, 3), (4, 5), ... of the rows 1 .. ny - 2.  The other nodes (the rows
 // 0 and ny - 1, and the columns 0, 1, nx - 1 and, for even nx, nx - 2) form the "edge"
-// set, stepped by the one-node code with the wall rules in a launch of its own.  The
-// in-place even step has no wall logic and runs every column pair (even nx).
+// set, stepped by the one-node code with the wall rules in the first block rows of the
+// same launch (its registers fit the pair code's budget), so that every 16-bit step is one
+// kernel and goes out as a programmatic dependent launch.  The in-place even step has no
+// wall logic and runs every column pair (even nx).
 #pragma once
 #include "lbm_kernels.cuh"
 
@@ -212,15 +214,76 @@ __host__ __device__ inline int inner_pairs(int nx) { return nx >= 5 ? (nx - 3) /
 // (256 B); numbered from column 2 instead, each warp's words started 4 bytes into a line,
 // so the first sector of every line of the two-buffer destination was written by two
 // warps in two parts.
-__device__ __forceinline__ bool inner_pair_of(const Geom& G, int& m, int& j) {
+__device__ __forceinline__ bool inner_pair_of(const Geom& G, int erows, int& m, int& j) {
     m = blockIdx.x * blockDim.x + threadIdx.x;
-    j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    j = 1 + ((int)blockIdx.y - erows) * blockDim.y + threadIdx.y;
     return m >= 1 && m <= inner_pairs(G.nx) && j <= G.ny - 2;
 }
 
+// The edge set of the pair kernels: rows 0 and ny - 1 (all columns), then for the rows
+// 1 .. ny - 2 the columns 0, 1, nx - 1 and, for even nx, nx - 2.
+__host__ __device__ inline int edge_cols(int nx) { return (nx & 1) ? 3 : 4; }
+__host__ __device__ inline long long edge_count(const Geom& G) {
+    return 2LL * G.nx + (long long)(G.ny - 2) * edge_cols(G.nx);
+}
+__device__ __forceinline__ void edge_node(const Geom& G, long long k, int& i, int& j) {
+    if (k < 2LL * G.nx) {
+        j = k < G.nx ? 0 : G.ny - 1;
+        i = (int)(k < G.nx ? k : k - G.nx);
+        return;
+    }
+    const int e = edge_cols(G.nx);
+    const long long r = k - 2LL * G.nx;
+    j = 1 + (int)(r / e);
+    const int c = (int)(r - (long long)(j - 1) * e);
+    i = c == 0 ? 0 : c == 1 ? 1 : c == 2 ? G.nx - 1 : G.nx - 2;
+}
+
+// The edge blocks of a pair launch: the first `erows` rows of its grid take the edge set,
+// one node per thread with the wall rules (first, so that their slower nodes do not form
+// the launch's tail); the pair rows follow.  Edge node k of block (bx, by) and thread t:
+// k = (by gridDim.x + bx) * threads + t.
+__device__ __forceinline__ long long edge_index() {
+    return ((long long)blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x * blockDim.y) +
+           threadIdx.y * blockDim.x + threadIdx.x;
+}
+
+// One-node steps of the edge set: the two-buffer pull and the in-place odd step.
+template <typename S>
+__device__ __forceinline__ void ab_edge_node(const S* __restrict__ src, S* __restrict__ dst,
+                                             float* __restrict__ hist, const Geom& G,
+                                             const Coef<float>& c, long long k) {
+    int i, j;
+    edge_node(G, k, i, j);
+    float f[9], g[5], h[5], hv[4];
+    const size_t self = (size_t)j * G.pitch + i;
+    gather_pull<false, true, false>(src, G, i, j, c, f, g, h);
+    load_hist(hist, G, self, hv);
+    uint32_t seed = node_seed(self, f[0], g[0]);
+    collide(c, f, g, h, hv);
+    store_ab(dst, G, self, c, f, g, h, seed);
+    store_hist(hist, G, self, hv);
+}
+
+template <typename S>
+__device__ __forceinline__ void aa_odd_edge_node(S* __restrict__ buf, float* __restrict__ hist,
+                                                 const Geom& G, const Coef<float>& c, long long k) {
+    int i, j;
+    edge_node(G, k, i, j);
+    float f[9], g[5], h[5], hv[4];
+    const size_t self = (size_t)j * G.pitch + i;
+    gather_pull<true, true, false>(buf, G, i, j, c, f, g, h);
+    load_hist(hist, G, self, hv);
+    uint32_t seed = node_seed(self, f[0], g[0]);
+    collide(c, f, g, h, hv);
+    store_aa_odd<false>(buf, G, i, j, self, c, f, g, h, seed);
+    store_hist(hist, G, self, hv);
+}
+
 // ---- kernels -------------------------------------------------------------------------
-// Two-buffer pull step of the inner column pairs: block (PAIR_BX, PAIR_BY) over
-// (1 + pairs, rows 1 .. ny - 2), the first thread of a row idle (inner_pair_of).
+// Two-buffer pull step: block (PAIR_BX, PAIR_BY) over (1 + pairs, erows + rows 1 .. ny - 2):
+// the edge blocks (edge_index), then the inner column pairs, the first thread of a row idle
+// (inner_pair_of).
 // Launch shape: 128 pairs per block, at least 5 blocks per SM (96 registers).  GB300,
 // 4096^2 BF16, us per step (two-buffer / in-place): 64 x 2 threads unbounded (118
 // registers) 342 / 317; 128 x 1 held to 5 blocks 324 / 302 (6 blocks spill: 336 / 315;
@@ -247,9 +310,16 @@ constexpr int PAIR_BX = LBM_PAIR_BX, PAIR_BY = LBM_PAIR_BY;
 template <typename S>
 __global__ void __launch_bounds__(PAIR_BX * PAIR_BY, LBM_PAIR_MIN_BLOCKS)
 step_ab_pair_kernel(const S* __restrict__ src, S* __restrict__ dst, float* __restrict__ hist, Geom G,
-                    Coef<f2> c) {
+                    Coef<f2> c, Coef<float> c1, int erows) {
+    pdl_trigger();
+    pdl_wait();                                // launched by launch_pdl()
+    if ((int)blockIdx.y < erows) {
+        const long long k = edge_index();
+        if (k < edge_count(G)) ab_edge_node(src, dst, hist, G, c1, k);
+        return;
+    }
     int m, j;
-    if (!inner_pair_of(G, m, j)) return;
+    if (!inner_pair_of(G, erows, m, j)) return;
     const size_t self = (size_t)j * G.pitch + 2 * m;
     f2 f[9], g[5], h[5], hv[4];
     gather_pair_pull<false, LBM_PAIR_AB_NC>(src, G, self, f, g, h);
@@ -268,6 +338,8 @@ step_ab_pair_kernel(const S* __restrict__ src, S* __restrict__ dst, float* __res
 template <typename S>
 __global__ void __launch_bounds__(PAIR_BX * PAIR_BY, LBM_PAIR_MIN_BLOCKS)
 step_aa_even_pair_kernel(S* __restrict__ buf, float* __restrict__ hist, Geom G, Coef<f2> c) {
+    pdl_trigger();
+    pdl_wait();                                // launched by launch_pdl()
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (2 * m >= G.nx || j >= G.ny) return;
@@ -284,13 +356,21 @@ step_aa_even_pair_kernel(S* __restrict__ buf, float* __restrict__ hist, Geom G, 
     store_hist_pair(hist, G, self, hv);
 }
 
-// In-place odd step of the inner column pairs (each thread reads and writes only its own
-// pair's locations, so the edge launch beside it touches disjoint memory).
+// In-place odd step: the edge blocks, then the inner column pairs (each thread reads and
+// writes only its own node's or pair's locations, so the two parts touch disjoint memory).
 template <typename S>
 __global__ void __launch_bounds__(PAIR_BX * PAIR_BY, LBM_PAIR_MIN_BLOCKS)
-step_aa_odd_pair_kernel(S* __restrict__ buf, float* __restrict__ hist, Geom G, Coef<f2> c) {
+step_aa_odd_pair_kernel(S* __restrict__ buf, float* __restrict__ hist, Geom G, Coef<f2> c,
+                        Coef<float> c1, int erows) {
+    pdl_trigger();
+    pdl_wait();                                // launched by launch_pdl()
+    if ((int)blockIdx.y < erows) {
+        const long long k = edge_index();
+        if (k < edge_count(G)) aa_odd_edge_node(buf, hist, G, c1, k);
+        return;
+    }
     int m, j;
-    if (!inner_pair_of(G, m, j)) return;
+    if (!inner_pair_of(G, erows, m, j)) return;
     const size_t self = (size_t)j * G.pitch + 2 * m;
     f2 f[9], g[5], h[5], hv[4];
     gather_pair_pull<true, true>(buf, G, self, f, g, h);
@@ -302,62 +382,6 @@ step_aa_odd_pair_kernel(S* __restrict__ buf, float* __restrict__ hist, Geom G, C
     collide_scalars(c, M, g, h, hv);
     store_pair_push_gh(buf, G, self, c.sr, g, h, state);
     store_hist_pair(hist, G, self, hv);
-}
-
-// The edge set of the pair kernels: rows 0 and ny - 1 (all columns), then for the rows
-// 1 .. ny - 2 the columns 0, 1, nx - 1 and, for even nx, nx - 2.
-__host__ __device__ inline int edge_cols(int nx) { return (nx & 1) ? 3 : 4; }
-__host__ __device__ inline long long edge_count(const Geom& G) {
-    return 2LL * G.nx + (long long)(G.ny - 2) * edge_cols(G.nx);
-}
-__device__ __forceinline__ void edge_node(const Geom& G, long long k, int& i, int& j) {
-    if (k < 2LL * G.nx) {
-        j = k < G.nx ? 0 : G.ny - 1;
-        i = (int)(k < G.nx ? k : k - G.nx);
-        return;
-    }
-    const int e = edge_cols(G.nx);
-    const long long r = k - 2LL * G.nx;
-    j = 1 + (int)(r / e);
-    const int c = (int)(r - (long long)(j - 1) * e);
-    i = c == 0 ? 0 : c == 1 ? 1 : c == 2 ? G.nx - 1 : G.nx - 2;
-}
-
-// One-node steps of the edge set, with the wall rules: the two-buffer pull and the
-// in-place odd step.
-template <typename S>
-__global__ void __launch_bounds__(128)
-step_ab_edge_kernel(const S* __restrict__ src, S* __restrict__ dst, float* __restrict__ hist, Geom G,
-                    Coef<float> c) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= edge_count(G)) return;
-    int i, j;
-    edge_node(G, k, i, j);
-    float f[9], g[5], h[5], hv[4];
-    const size_t self = (size_t)j * G.pitch + i;
-    gather_pull<false, true, false>(src, G, i, j, c, f, g, h);
-    load_hist(hist, G, self, hv);
-    uint32_t seed = node_seed(self, f[0], g[0]);
-    collide(c, f, g, h, hv);
-    store_ab(dst, G, self, c, f, g, h, seed);
-    store_hist(hist, G, self, hv);
-}
-
-template <typename S>
-__global__ void __launch_bounds__(128)
-step_aa_odd_edge_kernel(S* __restrict__ buf, float* __restrict__ hist, Geom G, Coef<float> c) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= edge_count(G)) return;
-    int i, j;
-    edge_node(G, k, i, j);
-    float f[9], g[5], h[5], hv[4];
-    const size_t self = (size_t)j * G.pitch + i;
-    gather_pull<true, true, false>(buf, G, i, j, c, f, g, h);
-    load_hist(hist, G, self, hv);
-    uint32_t seed = node_seed(self, f[0], g[0]);
-    collide(c, f, g, h, hv);
-    store_aa_odd<false>(buf, G, i, j, self, c, f, g, h, seed);
-    store_hist(hist, G, self, hv);
 }
 
 }  // namespace lbm

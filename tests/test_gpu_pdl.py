@@ -1,7 +1,8 @@
 """Programmatic dependent launches keep plain stream order.
 
 The steps that are one kernel (the FP32 two-buffer step, the in-place even step, the
-in-place odd step of small FP32 cavities, the batch's one-node tile step) go out as
+in-place odd step of small FP32 cavities, the 16-bit steps with two nodes per thread and
+their edge nodes in the same launch, the batch's one-node tile step) go out as
 programmatic dependent launches on the context's own stream: the next step's CTAs may be
 placed while the step before still runs, and each waits (griddepcontrol.wait) for that
 step to complete before it touches the state.  On the legacy default stream the library
@@ -20,8 +21,9 @@ KEYS = ("ux", "uy", "T", "C")
 LEGACY = 1          # cudaStreamLegacy: ordinary launches, no graphs
 
 
-def run(spec, layout, chunks, **kw):
-    c = lbm.Cavity(*spec.args(), precision="f32", layout=layout, seed=spec.seed, noise=spec.noise, **kw)
+def run(spec, layout, chunks, precision="f32", **kw):
+    c = lbm.Cavity(*spec.args(), precision=precision, layout=layout, seed=spec.seed, noise=spec.noise,
+                   **kw)
     reads = []
     c.residual()
     for n in chunks:
@@ -44,6 +46,23 @@ def test_cavity_programmatic_launches_equal_ordinary(layout, n):
         for k in KEYS:
             assert np.array_equal(got[k], ref[k]), (kw, k)
         assert reads == ref_reads, kw
+
+
+@pytest.mark.parametrize("precision", ["bf16", "f16"])
+@pytest.mark.parametrize("layout", ["ab", "aa"])
+def test_16bit_pair_steps_equal_ordinary(layout, precision):
+    """Two nodes per thread with the edge set in the first block rows of the same launch
+    (ragged: odd nx, and an even nx whose last pair column is an edge column)."""
+    for nx, ny in ((97, 41), (130, 67)):
+        spec = CavitySpec(nx, ny, Ra=1e5, Da=1e-2, eps=0.6, Le=2.0, N=-1.5, sigma=1.3, seed=8,
+                          noise=0.02)
+        chunks = [37, 128, 71]
+        ref, ref_reads = run(spec, layout, chunks, precision, stream=LEGACY)
+        for kw in ({}, {"graph_chunk": -1}):
+            got, reads = run(spec, layout, chunks, precision, **kw)
+            for k in KEYS:
+                assert np.array_equal(got[k], ref[k]), (nx, kw, k)
+            assert reads == ref_reads, (nx, kw)
 
 
 @pytest.mark.parametrize("layout", ["ab", "aa"])
