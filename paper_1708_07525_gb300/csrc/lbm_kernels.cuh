@@ -550,15 +550,11 @@ __device__ __forceinline__ void store_aa_odd_inner(S* __restrict__ buf, const Ge
     }
 }
 
-template <typename S, bool EXT>
-__global__ void __launch_bounds__(256)
-step_aa_odd_inner_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
-                         Coef<typename Real<S>::type> c) {
-    using R = typename Real<S>::type;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (!((unsigned)(i - 1) < (unsigned)(G.nx - 2) && (unsigned)(j - 1) < (unsigned)(G.ny - 2)))
-        return;
+// One node of the odd step's inner part (all eight neighbours in the cavity) and of its
+// ring of outermost nodes (ring_node(k), the general code with the wall rules).
+template <typename S, bool EXT, typename R>
+__device__ __forceinline__ void aa_odd_inner_node(S* __restrict__ buf, R* __restrict__ hist, const Geom& G,
+                                                  const Coef<R>& c, int i, int j) {
     R f[9], g[5], h[5], hv[4];
     const size_t self = (size_t)j * G.pitch + i;
     gather_pull_inner<true, true, true>(buf, G, self, f, g, h);
@@ -568,15 +564,9 @@ step_aa_odd_inner_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict
     store_aa_odd_inner(buf, G, self, c, f, g, h, seed);
     store_hist(hist, G, self, hv);
 }
-
-
-template <typename S, bool EXT>
-__global__ void __launch_bounds__(128)
-step_aa_odd_ring_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
-                        Coef<typename Real<S>::type> c) {
-    using R = typename Real<S>::type;
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= 2LL * G.nx + 2LL * (G.ny - 2)) return;
+template <typename S, bool EXT, typename R>
+__device__ __forceinline__ void aa_odd_ring_node(S* __restrict__ buf, R* __restrict__ hist, const Geom& G,
+                                                 const Coef<R>& c, long long k) {
     int i, j;
     ring_node(G, k, i, j);
     R f[9], g[5], h[5], hv[4];
@@ -587,6 +577,50 @@ step_aa_odd_ring_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict_
     collide_node<EXT>(c, self, G.plane, f, g, h, hv);
     store_aa_odd<EXT>(buf, G, i, j, self, c, f, g, h, seed);
     store_hist(hist, G, self, hv);
+}
+__host__ __device__ inline long long ring_count(const Geom& G) { return 2LL * G.nx + 2LL * (G.ny - 2); }
+
+template <typename S, bool EXT>
+__global__ void __launch_bounds__(256)
+step_aa_odd_inner_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
+                         Coef<typename Real<S>::type> c) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (!((unsigned)(i - 1) < (unsigned)(G.nx - 2) && (unsigned)(j - 1) < (unsigned)(G.ny - 2)))
+        return;
+    aa_odd_inner_node<S, EXT>(buf, hist, G, c, i, j);
+}
+
+template <typename S, bool EXT>
+__global__ void __launch_bounds__(128)
+step_aa_odd_ring_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
+                        Coef<typename Real<S>::type> c) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ring_count(G)) return;
+    aa_odd_ring_node<S, EXT>(buf, hist, G, c, k);
+}
+
+// The odd step as one launch: the first `rrows` block rows take the ring (node k =
+// (by gridDim.x + bx) * threads + t), the others the inner nodes (row j = by - rrows).
+// Held to the inner code's 64 registers (256 threads x 4 blocks); the ring code, which
+// alone takes 80, spills within that budget.
+template <typename S, bool EXT>
+__global__ void __launch_bounds__(256, 4)
+step_aa_odd_fused_kernel(S* __restrict__ buf, typename Real<S>::type* __restrict__ hist, Geom G,
+                         Coef<typename Real<S>::type> c, int rrows) {
+    pdl_trigger();
+    pdl_wait();                                // launched by launch_pdl()
+    if ((int)blockIdx.y < rrows) {
+        const long long k = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x * blockDim.y) +
+                            threadIdx.y * blockDim.x + threadIdx.x;
+        if (k < ring_count(G)) aa_odd_ring_node<S, EXT>(buf, hist, G, c, k);
+        return;
+    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = ((int)blockIdx.y - rrows) * blockDim.y + threadIdx.y;
+    if (!((unsigned)(i - 1) < (unsigned)(G.nx - 2) && (unsigned)(j - 1) < (unsigned)(G.ny - 2)))
+        return;
+    aa_odd_inner_node<S, EXT>(buf, hist, G, c, i, j);
 }
 
 // ---- initial state ---------------------------------------------------------------

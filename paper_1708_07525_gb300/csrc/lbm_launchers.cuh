@@ -129,6 +129,9 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
 #ifndef LBM_AA_SPLIT_MIN_NODES
 #define LBM_AA_SPLIT_MIN_NODES (1LL << 19)
 #endif
+#ifndef LBM_AA_ODD_FUSED
+#define LBM_AA_ODD_FUSED 1
+#endif
 
 template <typename S>
 cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
@@ -149,6 +152,22 @@ cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
         }
     }
     const long long split_min = std::is_same<R, double>::value ? 0 : LBM_AA_SPLIT_MIN_NODES;
+    if constexpr (std::is_same<R, float>::value && LBM_AA_ODD_FUSED) {
+        if (odd && G.nx >= 3 && G.ny >= 3 && (long long)G.nx * G.ny >= split_min) {
+            // ring and inner nodes in one programmatic dependent launch (the ring's block
+            // rows first)
+            const long long threads = (long long)b.x * b.y;
+            const long long rrows = ((ring_count(G) + threads - 1) / threads + gr.x - 1) / gr.x;
+            if (gr.y + rrows <= 65535) {
+                const dim3 gf(gr.x, (unsigned)(gr.y + rrows), 1);
+                if (ext)
+                    return launch_pdl(step_aa_odd_fused_kernel<S, true>, gf, b, L.stream, (S*)buf, (R*)hist, G,
+                                      c, (int)rrows);
+                return launch_pdl(step_aa_odd_fused_kernel<S, false>, gf, b, L.stream, (S*)buf, (R*)hist, G, c,
+                                  (int)rrows);
+            }
+        }
+    }
     if (odd && G.nx >= 3 && G.ny >= 3 && (long long)G.nx * G.ny >= split_min) {
         // the ring of outermost nodes beside the inner nodes (no wall logic); the two
         // launches touch disjoint locations
