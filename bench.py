@@ -336,7 +336,10 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",
-                     "kernel": (f"step_ab_kernel<{args.precision}> (inner nodes) + nee_ring_kernel"
+                     "kernel": ((f"step_ab_kernel<{args.precision}> (inner nodes) + nee_ring_kernel"
+                                 if args.precision == "f64" else
+                                 f"step_ab_nee_fused_kernel<{args.precision}> (wall ring and inner "
+                                 f"nodes in one launch)")
                                 if args.walls == "nee"
                                 else (f"step_{args.layout}_pair kernels<{args.precision}> (two "
                                       f"nodes per thread; edge nodes one per thread in the "

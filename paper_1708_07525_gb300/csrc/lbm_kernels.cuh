@@ -372,6 +372,24 @@ __device__ __forceinline__ void collide_node(const Coef<R>& c, size_t self, size
 }
 
 // ---- the fused step, two-buffer pull layout ---------------------------------------
+// One node of the two-buffer step; INNER: all eight neighbours in the cavity, no wall
+// logic compiled in.
+template <typename S, bool EXT, bool INNER, typename R>
+__device__ __forceinline__ void ab_node(const S* __restrict__ src, S* __restrict__ dst, R* __restrict__ hist,
+                                        const Geom& G, const Coef<R>& c, int i, int j) {
+    R f[9], g[5], h[5], hv[4];
+    const size_t self = (size_t)j * G.pitch + i;
+    if (INNER)
+        gather_pull_inner<false, true>(src, G, self, f, g, h);
+    else
+        gather_pull<false, true, EXT>(src, G, i, j, c, f, g, h);
+    load_hist(hist, G, self, hv);
+    uint32_t seed = Store<S>::kLow ? node_seed(self + c.seed_off, f[0], g[0]) : 0u;
+    collide_node<EXT>(c, self, G.plane, f, g, h, hv);
+    store_ab(dst, G, self, c, f, g, h, seed);
+    store_hist(hist, G, self, hv);
+}
+
 // EXT = true for cavities with moving walls or porous fields, false otherwise.
 // INNER = true: the outermost ring of nodes is left to nee_ring_kernel (walls with
 // nodes on them), so this kernel keeps the plain pull's registers and occupancy.
@@ -388,17 +406,7 @@ step_ab_kernel(const S* __restrict__ src, S* __restrict__ dst,
     if (i >= G.nx || j >= G.je) return;
     if (INNER && !((unsigned)(i - 1) < (unsigned)(G.nx - 2) && (unsigned)(j - 1) < (unsigned)(G.ny - 2)))
         return;
-    R f[9], g[5], h[5], hv[4];
-    const size_t self = (size_t)j * G.pitch + i;
-    if (INNER)
-        gather_pull_inner<false, true>(src, G, self, f, g, h);   // no wall logic compiled in
-    else
-        gather_pull<false, true, EXT>(src, G, i, j, c, f, g, h);
-    load_hist(hist, G, self, hv);
-    uint32_t seed = Store<S>::kLow ? node_seed(self + c.seed_off, f[0], g[0]) : 0u;
-    collide_node<EXT>(c, self, G.plane, f, g, h, hv);
-    store_ab(dst, G, self, c, f, g, h, seed);
-    store_hist(hist, G, self, hv);
+    ab_node<S, EXT, INNER>(src, dst, hist, G, c, i, j);
 }
 
 // Node k of the outermost ring, k = 0 .. 2 nx + 2 (ny - 2) - 1: bottom row, top row,
@@ -438,20 +446,14 @@ step_ab_ring_kernel(const S* __restrict__ src, S* __restrict__ dst,
 }
 
 // ---- the fused step with wall nodes (Sec. 3.3), two-buffer pull layout ---------------
-// The inner nodes take step_ab_kernel<S, EXT, true> (the plain pull); this kernel
+// The inner nodes take step_ab_kernel<S, EXT, true> (the plain pull); nee_ring_node
 // takes the ring of wall nodes, k = 0 .. 2 nx + 2 (ny - 2) - 1 (bottom row, top row,
 // left column, right column): populations rebuilt by Eqs. 33-35 from the
 // post-streaming populations of x_f and x_ff (both pulled from src, which no
 // launch of this step writes), then the same collision as every node.
-template <typename S>
-__global__ void __launch_bounds__(256)
-nee_ring_kernel(const S* __restrict__ src, S* __restrict__ dst,
-                typename Real<S>::type* __restrict__ hist, Geom G,
-                Coef<typename Real<S>::type> c) {
-    using R = typename Real<S>::type;
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nring = 2LL * G.nx + 2LL * (G.ny - 2);
-    if (k >= nring) return;
+template <typename S, typename R>
+__device__ __forceinline__ void nee_ring_node(const S* __restrict__ src, S* __restrict__ dst, R* __restrict__ hist,
+                                              const Geom& G, const Coef<R>& c, long long k) {
     int i, j;
     if (k < G.nx) {
         i = (int)k; j = 0;
@@ -470,6 +472,39 @@ nee_ring_kernel(const S* __restrict__ src, S* __restrict__ dst,
     collide_node<true>(c, self, G.plane, f, g, h, hv);
     store_ab(dst, G, self, c, f, g, h, seed);
     store_hist(hist, G, self, hv);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256)
+nee_ring_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                typename Real<S>::type* __restrict__ hist, Geom G,
+                Coef<typename Real<S>::type> c) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2LL * G.nx + 2LL * (G.ny - 2)) return;
+    nee_ring_node(src, dst, hist, G, c, k);
+}
+
+// The step with wall nodes as one launch: the first `rrows` block rows take the ring of
+// wall nodes (node k = (by gridDim.x + bx) * threads + t), the others the inner nodes
+// (row j = by - rrows) with the plain pull; held to the inner code's 64 registers.
+template <typename S, bool EXT>
+__global__ void __launch_bounds__(256, 4)
+step_ab_nee_fused_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                         typename Real<S>::type* __restrict__ hist, Geom G,
+                         Coef<typename Real<S>::type> c, int rrows) {
+    pdl_trigger();
+    pdl_wait();                                // launched by launch_pdl()
+    if ((int)blockIdx.y < rrows) {
+        const long long k = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x * blockDim.y) +
+                            threadIdx.y * blockDim.x + threadIdx.x;
+        if (k < 2LL * G.nx + 2LL * (G.ny - 2)) nee_ring_node(src, dst, hist, G, c, k);
+        return;
+    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = ((int)blockIdx.y - rrows) * blockDim.y + threadIdx.y;
+    if (!((unsigned)(i - 1) < (unsigned)(G.nx - 2) && (unsigned)(j - 1) < (unsigned)(G.ny - 2)))
+        return;
+    ab_node<S, EXT, true>(src, dst, hist, G, c, i, j);
 }
 
 // History (T u, C u) at t = 0 of the wall nodes, from their rebuilt initial state

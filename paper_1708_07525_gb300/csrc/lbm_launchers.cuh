@@ -51,6 +51,30 @@ inline bool pair_grid_aa_even(const Geom& G, dim3& gr) {
     return gr.y <= 65535u;
 }
 
+// With FP32 arithmetic the in-place odd step splits the inner nodes (no wall logic) from
+// the ring of outermost nodes from this many nodes on, below it runs as one kernel with
+// the wall logic for every node.  GB300, FP32, us per step over alternating odd and even
+// steps, one kernel / split with the ring on a second stream / split in one launch (the
+// ring's block rows first): 128^2 2.5 / 4.6 / 3.9, 256^2 2.9 / 4.9 / 4.6, 512^2 6.9 / 7.8 /
+// 6.3, 1024^2 28.2 / 27.5 / 25.5, 2048^2 121.3 / 117.0 / 114.6, 4096^2 - / 460.5 / 458.8.
+// FP64 splits at every size, the ring on a second stream (128^2 33.1 / 13.5 us, 1024^2
+// 507.5 / 502.3).
+#ifndef LBM_AA_SPLIT_MIN_NODES
+#define LBM_AA_SPLIT_MIN_NODES (1LL << 17)
+#endif
+// With FP32 arithmetic the split odd step is one launch (step_aa_odd_fused_kernel: the
+// ring's block rows, then the inner nodes), and so is the two-buffer step with wall nodes
+// (Sec. 3.3; step_ab_nee_fused_kernel): no second stream, no fork / join, a programmatic
+// dependent launch.  FP64 keeps the ring on a second stream beside the inner launch.  With
+// wall nodes, FP32, us per step (second stream / one launch): 1024^2 33.3 / 30.5, 4096^2
+// 459.2 / 456.7.
+#ifndef LBM_AA_ODD_FUSED
+#define LBM_AA_ODD_FUSED 1
+#endif
+#ifndef LBM_AB_NEE_FUSED
+#define LBM_AB_NEE_FUSED 1
+#endif
+
 template <typename S>
 cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G,
                            const Coef<typename Real<S>::type>& c, const LaunchCfg& L) {
@@ -74,6 +98,22 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
             // in one programmatic dependent launch
             return launch_pdl(step_ab_pair_kernel<S>, gp, dim3(PAIR_BX, PAIR_BY), L.stream, (const S*)src,
                               (S*)dst, (float*)hist, G, *L.pair, c, erows);
+    }
+    if constexpr (std::is_same<R, float>::value && LBM_AB_NEE_FUSED) {
+        if (c.nee) {
+            // the ring of wall nodes (the rebuild, Sec. 3.3) in the first block rows, the
+            // inner nodes (the plain pull) after them: one programmatic dependent launch
+            const long long threads = (long long)b.x * b.y;
+            const long long rrows = ((2LL * G.nx + 2LL * (G.ny - 2) + threads - 1) / threads + gr.x - 1) / gr.x;
+            if (gr.y + rrows <= 65535) {
+                const dim3 gf(gr.x, (unsigned)(gr.y + rrows), 1);
+                if (c.poro)
+                    return launch_pdl(step_ab_nee_fused_kernel<S, true>, gf, b, L.stream, (const S*)src, (S*)dst,
+                                      (R*)hist, G, c, (int)rrows);
+                return launch_pdl(step_ab_nee_fused_kernel<S, false>, gf, b, L.stream, (const S*)src, (S*)dst,
+                                  (R*)hist, G, c, (int)rrows);
+            }
+        }
     }
     if (c.nee) {
         // the ring of wall nodes: the rebuild (Sec. 3.3); inner nodes: the plain pull
@@ -119,19 +159,6 @@ cudaError_t launch_step_ab(const void* src, void* dst, void* hist, const Geom& G
     return launch_pdl(step_ab_kernel<S, false>, gr, b, L.stream, (const S*)src, (S*)dst, (R*)hist, G, c);
 }
 
-// With FP32 arithmetic the in-place odd step runs as two launches (inner nodes without
-// wall logic, and the ring of outermost nodes on a second stream) from this many nodes
-// on, below it as one kernel with the wall logic: in small cavities the second launch and
-// its fork / join cost more than the lighter inner kernel saves.  GB300, FP32, us per step
-// over alternating odd and even steps (one kernel / split): 128^2 2.5 / 4.6, 256^2 2.9 / 4.9, 512^2
-// 6.9 / 7.8, 1024^2 28.2 / 27.6, 2048^2 121.3 / 117.2.  FP64 splits at every size (128^2
-// 33.1 / 13.5 us, 1024^2 507.5 / 502.3).
-#ifndef LBM_AA_SPLIT_MIN_NODES
-#define LBM_AA_SPLIT_MIN_NODES (1LL << 19)
-#endif
-#ifndef LBM_AA_ODD_FUSED
-#define LBM_AA_ODD_FUSED 1
-#endif
 
 template <typename S>
 cudaError_t launch_step_aa(void* buf, void* hist, const Geom& G,
