@@ -1,8 +1,9 @@
 """Programmatic dependent launches keep plain stream order.
 
-The steps that are one kernel (the FP32 two-buffer step, the in-place even step, the
-in-place odd step of small FP32 cavities, the 16-bit steps with two nodes per thread and
-their edge nodes in the same launch, the batch's one-node tile step) go out as
+The steps that are one kernel (the FP32 two-buffer step, the in-place even step, the FP32
+in-place odd step with or without its ring of outermost nodes split into block rows of
+their own, the 16-bit steps with two nodes per thread and their edge nodes in the same
+launch, the batch's one-node tile step) go out as
 programmatic dependent launches on the context's own stream: the next step's CTAs may be
 placed while the step before still runs, and each waits (griddepcontrol.wait) for that
 step to complete before it touches the state.  On the legacy default stream the library
@@ -35,8 +36,9 @@ def run(spec, layout, chunks, precision="f32", **kw):
 @pytest.mark.parametrize("layout", ["ab", "aa"])
 @pytest.mark.parametrize("n", [96, 768], ids=["one-kernel-steps", "split-odd-step"])
 def test_cavity_programmatic_launches_equal_ordinary(layout, n):
-    # 96 x 51: every step one kernel; 768^2 (above 2^19 nodes): the in-place odd step is the
-    # inner + ring pair on two streams, the even step one kernel
+    # 96 x 51: every step one kernel with the wall logic for every node; 768^2 (above 2^17
+    # nodes): the in-place odd step runs the ring's block rows and the inner nodes in one
+    # launch
     spec = CavitySpec(n, n // 2 + 3 if n < 500 else n, Ra=1e5, Da=1e-2, eps=0.6, Le=2.0, N=-1.5,
                       sigma=1.3, seed=8, noise=0.02)
     chunks = [37, 128, 64, 71] if n < 500 else [37, 66]
