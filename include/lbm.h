@@ -394,8 +394,8 @@ lbm_status lbm_batch_set_tile(lbm_batch* b, int slot, int tile_w, int tile_h);
 
 /* L2 temporal blocking: cavities are grouped so that the per-step working sets
  * of the two groups in flight stay within l2_bytes (each group's within half of
- * it; 0 -> keep; default half the L2), and each group is advanced `steps` steps
- * (default 32) at a time, so that its state is read from L2 rather than HBM on
+ * it; 0 -> keep; default 3/8 of the L2), and each group is advanced `steps` steps
+ * (default 64) at a time, so that its state is read from L2 rather than HBM on
  * all but the first of them.  The groups are dealt alternately to the batch's
  * stream and a second stream the batch owns (forked from and joined back to
  * the batch's stream, also inside its CUDA graphs), so that one group's launches

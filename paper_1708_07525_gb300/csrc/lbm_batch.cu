@@ -205,8 +205,8 @@ struct lbm_batch {
     static constexpr int kLanes = 2;
     cudaStream_t lane[kLanes - 1] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[kLanes - 1] = {};
-    size_t l2_budget = 64u << 20;
-    int tblock = 32;
+    size_t l2_budget = 48u << 20;
+    int tblock = 64;
     bool dirty = true;
     int64_t t = 0;
     cudaStream_t stream = nullptr;
@@ -580,9 +580,11 @@ lbm_status lbm_batch_create(const lbm_instance* inst, int count, int capacity, s
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     int l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device);
-    // half of L2 for the groups in flight (GB300, 512 mixed cavities, two-buffer: 1/2
-    // beat 3/4 by 1 % and a whole L2 by 15 %)
-    if (l2 > 0) b->l2_budget = (size_t)l2 / 2;
+    // 3/8 of L2 for the groups in flight, 64 steps per block.  GB300, 512 mixed cavities,
+    // FP32 two-buffer / in place, GLUPS with programmatic dependent launches: 3/8 and 64
+    // steps 40.6 / 35.2, 1/2 and 32 steps 40.2 / 34.8, 3/4 39.3 / 28.4; below 3/8 the 256^2
+    // cavities exceed a lane's share and take the single-cavity kernels (1/4: 36.9 / 34.9).
+    if (l2 > 0) b->l2_budget = (size_t)l2 / 8 * 3;
     if (O.stream) {
         b->stream = (cudaStream_t)O.stream;
     } else {
