@@ -977,8 +977,21 @@ nush_tb_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c
 // order as the values do); the slots must be zero before the launch.  Block
 // (bx, by) takes the 256-column tiles bx, bx + gridDim.x, ... of the rows by,
 // by + gridDim.y, ...; with the grid of residual_grid() that is one node per thread.
+// Blocks per SM the residual pass is compiled for: its general gather with the wall rules
+// takes 90 registers left alone (2 blocks of 256 threads per SM, a quarter of the warp
+// slots, for a pass that is all loads).  GB300, 4096^2 FP32 two-buffer, ms per residual
+// call (at most 128 / 72 / 64 registers): 0.562 / 0.442 / 0.396.  The wall-node gather
+// would spill 112 bytes at 64 and takes 3 blocks (80 registers); FP64 is left alone.
+#ifndef LBM_RES_MIN_BLOCKS
+#define LBM_RES_MIN_BLOCKS 4
+#endif
+template <typename S, int MODE>
+constexpr int res_min_blocks() {
+    return sizeof(typename Real<S>::type) == 8 ? 1 : (MODE == GATHER_NEE_AB ? 3 : LBM_RES_MIN_BLOCKS);
+}
+
 template <typename S, bool EXT, typename P, int MODE>
-__global__ void __launch_bounds__(RES_THREADS)
+__global__ void __launch_bounds__(RES_THREADS, res_min_blocks<S, MODE>())
 residual_kernel(const S* __restrict__ buf, Geom G, Coef<typename Real<S>::type> c,
                 P* __restrict__ snap, unsigned long long* __restrict__ slots, int nslots) {
     using R = typename Real<S>::type;
