@@ -99,10 +99,11 @@ batch_step_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
 // The same step for tiles of exactly BATCH_THREADS nodes: one node per thread,
 // one tile per CTA and no loop, so nothing loop-invariant is hoisted into
 // registers (the descriptor stays in shared memory and occupancy stays high).
-// The two-buffer variant fits 64 registers without spilling (8 CTAs per SM
-// instead of 7).  The in-place one holds both parities' code (cavities in one
-// launch may be at different parities) and was compiled to 146 registers (3 CTAs
-// per SM) when left alone; held to 5 CTAs per SM it fits 96 without spilling.
+// The two-buffer variant is held to 64 registers (8 CTAs per SM instead of 7; 12
+// bytes of spills with the flow and scalar collisions as two calls).  The in-place
+// one holds both parities' code (cavities in one launch may be at different
+// parities) and was compiled to 146 registers (3 CTAs per SM) when left alone;
+// held to 5 CTAs per SM it fits 96 (24 bytes of spills).
 template <typename S, bool AA, bool NEE = false>
 __global__ void __launch_bounds__(BATCH_THREADS, NEE ? 1 : (AA ? 5 : 8))
 batch_step1_kernel(const BatchInst<typename Real<S>::type>* __restrict__ table,
