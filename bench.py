@@ -617,7 +617,7 @@ def run_batch(args):
     return 0
 
 
-def solve_alone(lbm, spec, precision, layout, stream, tol, nush_tol, check, cap):
+def solve_alone(lbm, spec, precision, layout, stream, tol, nush_tol, check, cap, round_nearest=False):
     """One cavity solve on its own (the single-cavity step kernels, CUDA graphs), stopped
     by the server's rule: at a check every `check` steps it is steady if the residual
     over those steps is below tol, or (from the second check on) if every Nu_L, Sh_L,
@@ -625,7 +625,7 @@ def solve_alone(lbm, spec, precision, layout, stream, tol, nush_tol, check, cap)
     steps it is unconverged; a non-finite value makes it diverged."""
     import numpy as np
     c = lbm.Cavity(*spec.args(), varpi=spec.varpi, precision=precision, layout=layout,
-                   seed=spec.seed, noise=spec.noise, stream=stream)
+                   seed=spec.seed, noise=spec.noise, stream=stream, round_nearest=round_nearest)
     prev = np.zeros(4)
     steps, checks, status, r, ns = 0, 0, 6, float("inf"), prev
     while True:
@@ -682,7 +682,8 @@ def run_serve(args):
 
     def serve(arrive):
         srv = lbm.Server(args.budget_gb * (1 << 30), max_slots=len(specs), check_every=check,
-                         precision=args.precision, layout=args.layout, stream=stream.cuda_stream)
+                         precision=args.precision, layout=args.layout, stream=stream.cuda_stream,
+                         round_nearest=args.round_nearest)
         t_start = time.perf_counter()
         pending = list(range(len(specs)))
         done = {}
@@ -726,7 +727,7 @@ def run_serve(args):
                 break
             t1 = time.perf_counter()
             res[k] = solve_alone(lbm, specs[k], precision, "ab", stream.cuda_stream, tol, ntol,
-                                 check, caps[k])
+                                 check, caps[k], args.round_nearest and precision != "f64")
             torch.cuda.synchronize()
             service.append(time.perf_counter() - t1)
             res[k]["seconds"] = service[-1]
@@ -796,6 +797,8 @@ def run_serve(args):
                                f"Nu/Sh moved < {ntol} relative, else at {args.max_steps} x L / 64 "
                                f"steps",
                    "precision": args.precision, "layout": args.layout,
+                   "rounding": ("to nearest" if args.round_nearest else "stochastic")
+                               if args.precision in ("bf16", "f16") else "n/a",
                    "budget_gb": args.budget_gb,
                    "grids": {str(n): sum(1 for s in specs if s.nx == n) for n in sizes},
                    "lattice_updates": int(sum(nodes[k] * served[k]["steps"] for k in served))},
@@ -1023,6 +1026,8 @@ def main():
     ap.add_argument("--check-every", type=int, default=500)
     ap.add_argument("--max-steps", type=int, default=300000)
     ap.add_argument("--budget-gb", type=float, default=8.0)
+    ap.add_argument("--round-nearest", action="store_true",
+                    help="serve: 16-bit storage rounded to nearest instead of stochastically")
     ap.add_argument("--plain-budget-s", type=float, default=300.0)
     ap.add_argument("--alone-budget-s", type=float, default=3600.0)
     ap.add_argument("--partial-out", default="")
