@@ -220,7 +220,12 @@ lbm_status lbm_create_raw(const lbm_params* params, const lbm_options* opt, lbm_
 lbm_status lbm_reset(lbm_ctx* ctx, const double* T_init, const double* C_init, uint64_t seed,
                      double noise);
 
-/* Advance n >= 0 time steps (asynchronous on the context's stream). */
+/* Advance n >= 0 time steps (asynchronous on the context's stream).  On a stream other
+ * than the legacy default stream the steps are replayed from CUDA graphs in chunks, and
+ * a step that is one kernel goes out as a programmatic dependent launch: its blocks may
+ * be placed while the kernel before it on the stream drains, but each waits for that
+ * kernel to complete before it touches the state, so work of the caller's on the same
+ * stream, before or after, is ordered as in plain stream order. */
 lbm_status lbm_step(lbm_ctx* ctx, int64_t n);
 
 /* Number of time steps taken since creation (or since the loaded checkpoint). */
