@@ -90,7 +90,8 @@ typedef struct {
     lbm_alloc_fn alloc;         /* NULL -> cudaMalloc / cudaFree */
     lbm_free_fn free;
     void* alloc_user;
-    int block_x, block_y;       /* launch tile of the step kernel; 0 -> tuned default */
+    int block_x, block_y;       /* launch tile of the step kernel: block_x a multiple of 32,
+                                   block_x * block_y <= 256; 0 -> tuned default */
     int graph_chunk;            /* steps per captured CUDA graph; 0 -> default, <0 -> off */
     const double* eps_field;    /* optional host [ny][nx] porosity field: the REV model with
                                    spatially varying eps (Sec. 2-3 applied per node, F_eps of

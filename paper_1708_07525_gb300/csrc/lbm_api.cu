@@ -569,9 +569,13 @@ lbm_status create_core(const lbm_params* params, const lbm_options* opt, int sla
         set_global_error("lbm_create: walls with nodes on them (nee) need the two-buffer layout");
         return LBM_ERR_INVALID;
     }
-    if (O.block_x < 0 || O.block_y < 0 || O.block_x * O.block_y > 1024 ||
-        (O.block_x && O.block_x % 32)) {
-        set_global_error("lbm_create: block_x must be a multiple of 32 and block_x*block_y <= 1024");
+    // the step kernels are compiled for blocks of at most 256 threads; the shape after
+    // the defaults below (block_x 0 -> 128 or 32, block_y 0 -> 128 / block_x) must fit
+    if (O.block_x < 0 || O.block_y < 0 || O.block_x > 256 || O.block_y > 256 ||
+        (O.block_x && O.block_x % 32) ||
+        (O.block_x ? O.block_x : (params->nx >= 128 ? 128 : 32)) *
+                (O.block_y ? O.block_y : 1) > 256) {
+        set_global_error("lbm_create: block_x must be a multiple of 32 and block_x*block_y <= 256");
         return LBM_ERR_INVALID;
     }
     lbm_ctx* c = new (std::nothrow) lbm_ctx();

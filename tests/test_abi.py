@@ -107,6 +107,17 @@ def test_nee_misuse_rejected():
         lbm.lbm_derive_params_nee(4, 16, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
 
 
+def test_block_shape_rejected_beyond_the_kernels_bounds():
+    """The step kernels take blocks of at most 256 threads; a larger or ragged launch tile
+    is refused at creation (before any device work), also where a zero (default) block_x
+    would make the tile too large."""
+    p = lbm.lbm_derive_params(256, 16, 1e4, 1e-2, 0.6, 1.0, 2.0, 1.0)
+    for block in ((512, 1), (128, 4), (48, 1), (0, 4), (256, 2)):
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.Cavity(params=p, block=block, allocator=None)
+        assert ei.value.status == lbm.ERR_INVALID, block
+
+
 def test_derive_lid_nee_matches_the_oracle(oracle_mod):
     g = lbm.lbm_derive_params_lid_nee(129, 129, 100.0, 1e2, 0.1, 0.95, 1.0, 1.0, -500.0)
     o = oracle_mod.derive_lid(129, 129, 100.0, 1e2, 0.1, 0.95, 1.0, 1.0, -500.0, nee=True)
