@@ -210,14 +210,17 @@ def run_reference(args):
 
 
 def step_launches(args, k):
-    """Kernels launched by k time steps of one cavity: one fused kernel per step, except
-    where the step is split into an inner-node kernel and a ring kernel (wall nodes; the
-    two-buffer layout with FP64 or 16-bit storage; the odd steps of the in-place layout)."""
+    """Kernels launched by k time steps of the benchmark cavity.  With FP32 arithmetic
+    (FP32 and 16-bit storage) every step is one launch: the FP32 steps, the in-place odd
+    step with its ring in the same launch, the step with wall nodes with its wall ring in
+    the same launch, the 16-bit pair steps with their edge set.  FP64 splits the two-buffer
+    step (also with wall nodes) and the in-place odd step into an inner-node launch and a
+    ring launch on a second stream."""
+    if args.precision != "f64":
+        return k
     if args.layout == "aa":
         return k + k // 2
-    if args.walls == "nee" or args.precision != "f32":
-        return 2 * k
-    return k
+    return 2 * k
 
 
 def run_ours(args):
